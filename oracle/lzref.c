@@ -1,0 +1,308 @@
+/*
+ * lzref.c -- CPU oracle for chunked multi-byte LZSS.  TEST INFRASTRUCTURE
+ * ONLY (see lzref.h): the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark call it; the product never does.
+ *
+ * Everything here is the plain definition, written for a reader to check
+ * against the paper by eye: no blocking, no hashing, no early exits that
+ * the definition does not have.  Cost is O(k * W * len) per chunk.
+ */
+#include "lzref.h"
+
+#include <stdlib.h>
+#include <string.h>
+
+enum { REF_OK = 0, REF_EINVAL = 1, REF_ESMALL = 2, REF_ECORRUPT = 3 };
+
+#define REF_HEADER_BYTES 32u
+#define REF_TABLE_ENTRY 8u
+#define REF_INDEX_STRIDE 64u
+
+/* Parameter set (one reading of section 3.2.3 and Table 1's grid):
+ *   S (symbol bytes) in {1,2,4}; C (chunk bytes) a multiple of 16 in
+ *   [16, 32768]; W (window, symbols) in [1, 1024]; 1 <= m <= M <= 255,
+ *   M fitting the one-byte length field of section 3.3.2. */
+int lzref_check_params(uint32_t S, uint32_t C, uint32_t W, uint32_t m,
+                       uint32_t M) {
+  if (S != 1 && S != 2 && S != 4) return REF_EINVAL;
+  if (C < 16 || C > 32768 || C % 16 != 0) return REF_EINVAL;
+  if (W < 1 || W > 1024) return REF_EINVAL;
+  if (m < 1 || m > M || M > 255) return REF_EINVAL;
+  return REF_OK;
+}
+
+/* Offset field width: one byte while every offset-1 fits in 8 bits. */
+static uint32_t ref_off_bytes(uint32_t W) { return W <= 256 ? 1u : 2u; }
+
+static uint64_t ref_div_up(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+/* Worst-case record of a chunk of k symbols: flags for k tokens plus the
+ * largest payload a parse can have.  A parse with `lit` literal symbols
+ * and the rest covered by pointers of >= m symbols has payload
+ * S*lit + (1+offB)*floor((k-lit)/m); its maximum over lit is
+ * S*k + max(0, 1+offB-S*m)*floor(k/m). */
+static uint64_t ref_record_bound(uint64_t k, uint32_t S, uint32_t offB,
+                                 uint32_t m) {
+  uint64_t extra = (1u + offB > S * m) ? (1u + offB - S * m) : 0u;
+  return ref_div_up(k, 8) + (uint64_t)S * k + extra * (k / m);
+}
+
+uint64_t lzref_bound(uint64_t n, uint32_t S, uint32_t C, uint32_t W,
+                     uint32_t m, uint32_t M) {
+  if (lzref_check_params(S, C, W, m, M) != REF_OK) return 0;
+  uint64_t nc = ref_div_up(n, C);
+  uint64_t total = REF_HEADER_BYTES + REF_TABLE_ENTRY * nc +
+                   8u * ref_div_up(nc, REF_INDEX_STRIDE);
+  uint32_t offB = ref_off_bytes(W);
+  for (uint64_t c = 0; c < nc; ++c) {
+    uint64_t bytes = (c + 1 < nc) ? C : n - c * (uint64_t)C;
+    total += ref_record_bound(bytes / S, S, offB, m);
+  }
+  return total;
+}
+
+/* Symbols i and j of a chunk are equal iff their S bytes are equal. */
+static int ref_sym_eq(const uint8_t *chunk, uint32_t S, uint32_t i,
+                      uint32_t j) {
+  return memcmp(chunk + (size_t)i * S, chunk + (size_t)j * S, S) == 0;
+}
+
+/* Section 2.2 step 2, over S-byte symbols (section 3.2.3):
+ * for every offset d = 1 .. min(W, p) extend the match symbol by symbol
+ * while it stays within min(M, d, k-p) symbols (a pointer may not run into
+ * the coding position, section 3.3.2); keep the first d that reaches the
+ * largest length, which is the nearest one. */
+void lzref_longest_match(const uint8_t *chunk, uint32_t k, uint32_t p,
+                         uint32_t S, uint32_t W, uint32_t M, uint32_t *len,
+                         uint32_t *off) {
+  uint32_t best = 0, best_d = 0;
+  uint32_t dmax = W < p ? W : p;
+  for (uint32_t d = 1; d <= dmax; ++d) {
+    uint32_t cap = M;
+    if (d < cap) cap = d;
+    if (k - p < cap) cap = k - p;
+    uint32_t l = 0;
+    while (l < cap && ref_sym_eq(chunk, S, p + l, p - d + l)) ++l;
+    if (l > best) {
+      best = l;
+      best_d = d;
+    }
+  }
+  *len = best;
+  *off = best_d;
+}
+
+/* Section 2.2 steps 1, 3, 4, 6: greedy parse from the chunk start. */
+uint32_t lzref_parse_chunk(const uint8_t *chunk, uint32_t k, uint32_t S,
+                           uint32_t W, uint32_t m, uint32_t M,
+                           uint32_t *tok_len, uint32_t *tok_off) {
+  uint32_t p = 0, t = 0;
+  while (p < k) {
+    uint32_t len, off;
+    lzref_longest_match(chunk, k, p, S, W, M, &len, &off);
+    if (len >= m) {
+      tok_len[t] = len;
+      tok_off[t] = off;
+      p += len;
+    } else {
+      tok_len[t] = 1;
+      tok_off[t] = 0;
+      p += 1;
+    }
+    ++t;
+  }
+  return t;
+}
+
+static void ref_put_u32(uint8_t *dst, uint32_t v) {
+  for (int i = 0; i < 4; ++i) dst[i] = (uint8_t)(v >> (8 * i));
+}
+static void ref_put_u64(uint8_t *dst, uint64_t v) {
+  for (int i = 0; i < 8; ++i) dst[i] = (uint8_t)(v >> (8 * i));
+}
+static uint32_t ref_get_u32(const uint8_t *src) {
+  uint32_t v = 0;
+  for (int i = 0; i < 4; ++i) v |= (uint32_t)src[i] << (8 * i);
+  return v;
+}
+static uint64_t ref_get_u64(const uint8_t *src) {
+  uint64_t v = 0;
+  for (int i = 0; i < 8; ++i) v |= (uint64_t)src[i] << (8 * i);
+  return v;
+}
+
+int lzref_compress(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
+                   uint32_t W, uint32_t m, uint32_t M, uint8_t *out,
+                   uint64_t cap, uint64_t *out_bytes) {
+  if (lzref_check_params(S, C, W, m, M) != REF_OK) return REF_EINVAL;
+  if (n % S != 0) return REF_EINVAL;
+  uint64_t nc = ref_div_up(n, C);
+  if (nc > 0xFFFFFFFFull) return REF_EINVAL;
+  uint32_t offB = ref_off_bytes(W);
+  uint64_t n_index = ref_div_up(nc, REF_INDEX_STRIDE);
+  uint64_t table_at = REF_HEADER_BYTES;
+  uint64_t index_at = table_at + REF_TABLE_ENTRY * nc;
+  uint64_t records_at = index_at + 8u * n_index;
+  if (cap < records_at) return REF_ESMALL;
+
+  memset(out, 0, (size_t)records_at);
+  memcpy(out, "GLZ1", 4);
+  out[4] = 1;
+  out[5] = (uint8_t)S;
+  out[6] = (uint8_t)offB;
+  out[7] = (uint8_t)m;
+  out[8] = (uint8_t)M;
+  ref_put_u32(out + 12, C);
+  ref_put_u32(out + 16, W);
+  ref_put_u32(out + 20, (uint32_t)nc);
+  ref_put_u64(out + 24, n);
+
+  uint32_t kmax = C / S;
+  uint32_t *tok_len = (uint32_t *)malloc(sizeof(uint32_t) * kmax);
+  uint32_t *tok_off = (uint32_t *)malloc(sizeof(uint32_t) * kmax);
+  if (!tok_len || !tok_off) {
+    free(tok_len);
+    free(tok_off);
+    return REF_EINVAL;
+  }
+
+  uint64_t pos = records_at; /* write cursor (absolute) */
+  int rc = REF_OK;
+  for (uint64_t c = 0; c < nc; ++c) {
+    const uint8_t *chunk = in + c * (uint64_t)C;
+    uint64_t bytes = (c + 1 < nc) ? C : n - c * (uint64_t)C;
+    uint32_t k = (uint32_t)(bytes / S);
+    uint32_t ntok = lzref_parse_chunk(chunk, k, S, W, m, M, tok_len, tok_off);
+
+    if (c % REF_INDEX_STRIDE == 0)
+      ref_put_u64(out + index_at + 8u * (c / REF_INDEX_STRIDE),
+                  pos - records_at);
+
+    uint32_t flag_bytes = (ntok + 7) / 8;
+    uint64_t payload = 0;
+    for (uint32_t t = 0; t < ntok; ++t)
+      payload += tok_off[t] ? 1u + offB : S;
+    ref_put_u32(out + table_at + REF_TABLE_ENTRY * c, ntok);
+    ref_put_u32(out + table_at + REF_TABLE_ENTRY * c + 4, (uint32_t)payload);
+
+    if (pos + flag_bytes + payload > cap) {
+      rc = REF_ESMALL;
+      break;
+    }
+    uint8_t *flags = out + pos;
+    memset(flags, 0, flag_bytes);
+    uint8_t *pay = flags + flag_bytes;
+    uint32_t p = 0; /* symbol cursor inside the chunk */
+    for (uint32_t t = 0; t < ntok; ++t) {
+      if (tok_off[t]) {
+        flags[t >> 3] |= (uint8_t)(1u << (t & 7));
+        *pay++ = (uint8_t)tok_len[t];
+        uint32_t stored = tok_off[t] - 1;
+        *pay++ = (uint8_t)(stored & 0xFF);
+        if (offB == 2) *pay++ = (uint8_t)(stored >> 8);
+      } else {
+        memcpy(pay, chunk + (size_t)p * S, S);
+        pay += S;
+      }
+      p += tok_len[t];
+    }
+    pos += flag_bytes + payload;
+  }
+  free(tok_len);
+  free(tok_off);
+  if (rc != REF_OK) return rc;
+  *out_bytes = pos;
+  return REF_OK;
+}
+
+/* Header checks shared by both decoder entry points. */
+static int ref_read_header(const uint8_t *in, uint64_t in_bytes,
+                           uint32_t *S, uint32_t *offB, uint32_t *C,
+                           uint32_t *W, uint32_t *m, uint32_t *M,
+                           uint64_t *nc, uint64_t *n) {
+  if (in_bytes < REF_HEADER_BYTES) return REF_ECORRUPT;
+  if (memcmp(in, "GLZ1", 4) != 0 || in[4] != 1) return REF_ECORRUPT;
+  if (in[9] || in[10] || in[11]) return REF_ECORRUPT;
+  *S = in[5];
+  *offB = in[6];
+  *m = in[7];
+  *M = in[8];
+  *C = ref_get_u32(in + 12);
+  *W = ref_get_u32(in + 16);
+  *nc = ref_get_u32(in + 20);
+  *n = ref_get_u64(in + 24);
+  if (lzref_check_params(*S, *C, *W, *m, *M) != REF_OK) return REF_ECORRUPT;
+  if (*offB != ref_off_bytes(*W)) return REF_ECORRUPT;
+  if (*n % *S != 0) return REF_ECORRUPT;
+  if (*nc != ref_div_up(*n, *C)) return REF_ECORRUPT;
+  return REF_OK;
+}
+
+int lzref_decompressed_size(const uint8_t *in, uint64_t in_bytes,
+                            uint64_t *n) {
+  uint32_t S, offB, C, W, m, M;
+  uint64_t nc;
+  int rc = ref_read_header(in, in_bytes, &S, &offB, &C, &W, &m, &M, &nc, n);
+  return rc;
+}
+
+/* Inverse of lzref_compress.  Pointers are copied symbol by symbol in
+ * token order, so a source that is itself pointer output is already in
+ * place when it is read. */
+int lzref_decompress(const uint8_t *in, uint64_t in_bytes, uint8_t *out,
+                     uint64_t cap, uint64_t *out_bytes) {
+  uint32_t S, offB, C, W, m, M;
+  uint64_t nc, n;
+  int rc = ref_read_header(in, in_bytes, &S, &offB, &C, &W, &m, &M, &nc, &n);
+  if (rc != REF_OK) return rc;
+  uint64_t n_index = ref_div_up(nc, REF_INDEX_STRIDE);
+  uint64_t table_at = REF_HEADER_BYTES;
+  uint64_t index_at = table_at + REF_TABLE_ENTRY * nc;
+  uint64_t records_at = index_at + 8u * n_index;
+  if (in_bytes < records_at) return REF_ECORRUPT;
+  if (cap < n) return REF_ESMALL;
+
+  uint64_t pos = records_at;
+  for (uint64_t c = 0; c < nc; ++c) {
+    if (c % REF_INDEX_STRIDE == 0 &&
+        ref_get_u64(in + index_at + 8u * (c / REF_INDEX_STRIDE)) !=
+            pos - records_at)
+      return REF_ECORRUPT;
+    uint32_t ntok = ref_get_u32(in + table_at + REF_TABLE_ENTRY * c);
+    uint32_t payload = ref_get_u32(in + table_at + REF_TABLE_ENTRY * c + 4);
+    uint64_t flag_bytes = ((uint64_t)ntok + 7) / 8;
+    if (pos + flag_bytes + payload > in_bytes) return REF_ECORRUPT;
+    const uint8_t *flags = in + pos;
+    const uint8_t *pay = flags + flag_bytes;
+    const uint8_t *pay_end = pay + payload;
+    uint8_t *dst = out + c * (uint64_t)C;
+    uint64_t bytes = (c + 1 < nc) ? C : n - c * (uint64_t)C;
+    uint32_t k = (uint32_t)(bytes / S);
+    uint32_t p = 0;
+    for (uint32_t t = 0; t < ntok; ++t) {
+      if (p >= k) return REF_ECORRUPT;
+      if ((flags[t >> 3] >> (t & 7)) & 1u) {
+        if (pay + 1 + offB > pay_end) return REF_ECORRUPT;
+        uint32_t len = pay[0];
+        uint32_t off = pay[1];
+        if (offB == 2) off |= (uint32_t)pay[2] << 8;
+        off += 1;
+        pay += 1 + offB;
+        if (len == 0 || off > p || len > k - p) return REF_ECORRUPT;
+        for (uint32_t i = 0; i < len; ++i)
+          memcpy(dst + (size_t)(p + i) * S, dst + (size_t)(p + i - off) * S,
+                 S);
+        p += len;
+      } else {
+        if (pay + S > pay_end) return REF_ECORRUPT;
+        memcpy(dst + (size_t)p * S, pay, S);
+        pay += S;
+        p += 1;
+      }
+    }
+    if (p != k || pay != pay_end) return REF_ECORRUPT;
+    pos += flag_bytes + payload;
+  }
+  *out_bytes = n;
+  return REF_OK;
+}
