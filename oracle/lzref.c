@@ -288,7 +288,9 @@ int lzref_decompress(const uint8_t *in, uint64_t in_bytes, uint8_t *out,
         if (offB == 2) off |= (uint32_t)pay[2] << 8;
         off += 1;
         pay += 1 + offB;
-        if (len == 0 || off > p || len > k - p) return REF_ECORRUPT;
+        /* an offset reaches at most W symbols back (section 2.2 sliding window)
+         and never before the chunk start */
+        if (len == 0 || off > p || off > W || len > k - p) return REF_ECORRUPT;
         for (uint32_t i = 0; i < len; ++i)
           memcpy(dst + (size_t)(p + i) * S, dst + (size_t)(p + i - off) * S,
                  S);

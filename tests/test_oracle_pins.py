@@ -321,6 +321,8 @@ def test_decoder_rejects_corruption():
     first = st.records_at
     b = bytearray(good); b[first + 2 + 3 + 1] = 200; cases.append(b)  # offset 201 > p
     b = bytearray(good); b[first + 2 + 3] = 0; cases.append(b)        # length 0
+    # offset beyond the window: W=8, last pointer (6,6) of chunk 0 -> offset 9
+    b = bytearray(good); b[first + 2 + 3 + 2 + 1] = 8; cases.append(b)
     b = bytearray(good); b[st.records_at - 8] = 1; cases.append(b)    # index
     for i, c in enumerate(cases):
         assert oracle.decompress_status(bytes(c)) == oracle.ECORRUPT, i
