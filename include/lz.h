@@ -1,0 +1,138 @@
+/*
+ * lz.h -- C ABI of the GB300 (sm_103a) chunked multi-byte LZSS codec.
+ *
+ * Method: gpuLZ (ICS'23).  Compression is LZSS (section 2.2: greedy longest
+ * match in a sliding window, pointer or literal, one flag bit per token)
+ * over S-byte symbols (section 3.2.3), on independent chunks (section
+ * 3.3.1), with the output offsets found by a two-pass prefix sum -- local
+ * inside a chunk, then global over chunks (section 3.2.2) -- fused into the
+ * matching/encoding kernel (section 3.3.2; the separate scan and deflate
+ * kernels of sections 3.3.3/3.3.4 are folded into it).
+ *
+ * The parse is the exact greedy one: at each coding position the longest
+ * match over offsets 1..min(W, p) (lengths bounded by M, by the offset and
+ * by the symbols left in the chunk), the nearest offset on ties; a pointer
+ * when its length is >= m, else a literal.  Output is byte-identical to the
+ * CPU definition for the same parameters.
+ *
+ * Stream layout "GLZ1" (all integers little-endian):
+ *   header  32 B: "GLZ1", u8 version (1), u8 S, u8 offB, u8 m, u8 M,
+ *           3 zero bytes, u32 chunk_bytes, u32 W, u32 n_chunks, u64 n_bytes
+ *   table   n_chunks x {u32 n_tokens, u32 payload_bytes}
+ *   index   ceil(n_chunks/64) x u64: offset of the record of chunk 64*j,
+ *           relative to the start of the records region
+ *   records per chunk: ceil(n_tokens/8) flag bytes (token t = bit t&7 of
+ *           byte t>>3; 1 = pointer), then the payload: a literal is its S
+ *           bytes, a pointer is u8 length then (offset-1) as u8 (offB = 1,
+ *           W <= 256) or u16 (offB = 2).  Lengths and offsets count symbols.
+ *
+ * Conventions for every entry point below:
+ *   - Pointers named d_* are device pointers (cudaMalloc, cudaMallocAsync,
+ *     or a torch CUDA tensor's data pointer) on the context's device; the
+ *     caller owns them.  h_* pointers are host pointers.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) and perform no host synchronisation, except
+ *     lz_decompressed_size and lz_sync, which say so.
+ *   - Argument errors are returned synchronously and nothing is enqueued.
+ *   - Errors found on the device (output too small, corrupt stream,
+ *     bounded device wait expired) are sticky in the context and returned
+ *     (then cleared) by lz_sync.
+ *   - A context serialises its work through one scratch area: calls that
+ *     share a context must be ordered on one stream (use one context per
+ *     concurrent stream).
+ */
+#ifndef GB300_LZ_H
+#define GB300_LZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *lz_stream_t; /* same type as cudaStream_t */
+
+typedef struct lz_params {
+  uint32_t symbol_bytes; /* S: 1, 2 or 4 (section 3.2.3)                 */
+  uint32_t chunk_bytes;  /* C: multiple of 16 in [16, 32768] (3.3.1)     */
+  uint32_t window;       /* W: 1..1024 symbols (section 2.2, 3.2.3)      */
+  uint32_t min_match;    /* m: 1..max_match (minimum pointer length)     */
+  uint32_t max_match;    /* M: min_match..255 (one length byte, 3.3.2)   */
+} lz_params;
+
+typedef enum lz_status {
+  LZ_OK = 0,
+  LZ_ERR_INVALID_ARG = 1,      /* bad pointer, size or parameter          */
+  LZ_ERR_BUFFER_TOO_SMALL = 2, /* output capacity below what is needed    */
+  LZ_ERR_CORRUPT = 3,          /* input is not a well-formed GLZ1 stream  */
+  LZ_ERR_NOMEM = 4,            /* context scratch allocation failed       */
+  LZ_ERR_CUDA = 5,             /* CUDA runtime error (launch, copy, ...)  */
+  LZ_ERR_TIMEOUT = 6           /* a bounded device-side wait gave up      */
+} lz_status;
+
+typedef struct lz_ctx lz_ctx;
+
+/* Create a context on `device` (cudaSetDevice is called on it).  The
+ * context owns a small device scratch area (chunk status words for the
+ * global scan, a work counter, the sticky error word).  Returns
+ * LZ_ERR_INVALID_ARG for a null ctx or bad device, LZ_ERR_NOMEM or
+ * LZ_ERR_CUDA on allocation failure. */
+lz_status lz_create(lz_ctx **ctx, int device);
+
+/* Free a context (synchronises the device first).  NULL is ignored. */
+void lz_destroy(lz_ctx *ctx);
+
+/* Human-readable name of a status code (static string). */
+const char *lz_status_string(lz_status s);
+
+/* LZ_OK if *p is a valid parameter set, else LZ_ERR_INVALID_ARG. */
+lz_status lz_check_params(const lz_params *p);
+
+/* Pure host function: the largest stream lz_compress can produce for
+ * n_bytes of input with parameters *p, i.e. header + table + index + per
+ * chunk ceil(k/8) + S*k + max(0, 1+offB-S*m)*floor(k/m) (k = symbols in the
+ * chunk).  Returns 0 if *p is invalid. */
+uint64_t lz_compressed_bound(uint64_t n_bytes, const lz_params *p);
+
+/* Compress n_bytes at d_in (n_bytes % S == 0; n_bytes == 0 allowed) into
+ * d_out (capacity out_cap bytes) and store the stream size in *d_out_bytes
+ * (a device uint64, 8-byte aligned).  One kernel launch (plus a scratch
+ * clear); d_in is staged with TMA bulk copies when it is 16-byte aligned.
+ * Returns LZ_ERR_BUFFER_TOO_SMALL synchronously when out_cap cannot even
+ * hold header + table + index; if the records do not fit, the stream is
+ * incomplete, *d_out_bytes still receives the size that was needed and
+ * lz_sync reports LZ_ERR_BUFFER_TOO_SMALL.  Capacity
+ * lz_compressed_bound(n_bytes, p) always suffices. */
+lz_status lz_compress(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
+                      const lz_params *p, void *d_out, uint64_t out_cap,
+                      uint64_t *d_out_bytes, lz_stream_t stream);
+
+/* Read and validate the header of the stream at d_in (in_bytes long) and
+ * return its decompressed size in *h_n.  Synchronises `stream` (it copies
+ * the 32-byte header to the host).  LZ_ERR_CORRUPT for a bad header. */
+lz_status lz_decompressed_size(const void *d_in, uint64_t in_bytes,
+                               uint64_t *h_n, lz_stream_t stream);
+
+/* Decompress the stream at d_in (in_bytes long) into d_out (capacity
+ * out_cap bytes) and store the output size in *d_out_bytes (device
+ * uint64).  Nothing about the stream needs to be known on the host: the
+ * kernel reads the header, table and index itself.  Structural errors
+ * (bad header, truncated record, offset before the chunk start or beyond
+ * the window, token overrun, payload size mismatch, inconsistent index)
+ * are reported as LZ_ERR_CORRUPT and out_cap < n_bytes as
+ * LZ_ERR_BUFFER_TOO_SMALL, both by lz_sync.  in_bytes < 32 is rejected
+ * synchronously with LZ_ERR_CORRUPT. */
+lz_status lz_decompress(lz_ctx *ctx, const void *d_in, uint64_t in_bytes,
+                        void *d_out, uint64_t out_cap, uint64_t *d_out_bytes,
+                        lz_stream_t stream);
+
+/* Synchronise `stream`, then return and clear the context's sticky device
+ * error (LZ_OK if none).  When several errors occurred the most severe is
+ * returned: TIMEOUT, then CORRUPT, then BUFFER_TOO_SMALL. */
+lz_status lz_sync(lz_ctx *ctx, lz_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_LZ_H */

@@ -1,0 +1,287 @@
+// decompress.cu -- the decompression kernel (one warp per chunk).
+//
+// The paper only reports decompression throughput (section 4.4) and gives
+// no algorithm; this is the design used here.  The host knows nothing
+// about the stream: every warp reads and checks the header itself, so the
+// call needs no host synchronisation.  Per chunk:
+//   * the record offset is the superblock index entry plus the record sizes
+//     of the (at most 63) chunks before it in its superblock -- no scan
+//     across the whole stream;
+//   * tokens are decoded 32 at a time (lane = token): the flag bits give
+//     each token's payload offset by popcount, a shuffle scan of token
+//     lengths gives each token's output position;
+//   * output positions are then produced 32 at a time (lane = position):
+//     the owning token is found by a binary search over the 32 token start
+//     positions (shuffles); a position inside a pointer copies from
+//     position - offset, and chains whose source lies in the same 32
+//     positions are resolved by pointer jumping (five shuffle rounds);
+//     older sources are read from a ring of the last >= W+32 decoded
+//     symbols in shared memory (offsets are at most W);
+//   * symbols are stored straight to the output, 32*S contiguous bytes per
+//     warp instruction.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "glz_common.h"
+#include "glz_device.cuh"
+
+namespace glz {
+
+namespace {
+
+struct Header {
+  uint32_t S, offB, m, M, C, W, nc;
+  uint64_t n;
+};
+
+__device__ __forceinline__ bool read_header(const uint8_t *in, Header &h) {
+  const bool magic = in[0] == 'G' && in[1] == 'L' && in[2] == 'Z' &&
+                     in[3] == '1' && in[4] == 1 && in[9] == 0 && in[10] == 0 &&
+                     in[11] == 0;
+  h.S = in[5];
+  h.offB = in[6];
+  h.m = in[7];
+  h.M = in[8];
+  h.C = static_cast<uint32_t>(ld_le(in + 12, 4));
+  h.W = static_cast<uint32_t>(ld_le(in + 16, 4));
+  h.nc = static_cast<uint32_t>(ld_le(in + 20, 4));
+  h.n = ld_le(in + 24, 8);
+  bool ok = magic && (h.S == 1 || h.S == 2 || h.S == 4);
+  ok = ok && h.C >= 16 && h.C <= kMaxChunk && h.C % 16 == 0;
+  ok = ok && h.W >= 1 && h.W <= kMaxWindow;
+  ok = ok && h.m >= 1 && h.m <= h.M && h.M <= 255;
+  ok = ok && h.offB == (h.W <= 256 ? 1u : 2u);
+  ok = ok && h.n % h.S == 0;
+  ok = ok && static_cast<uint64_t>(h.nc) == (h.n + h.C - 1) / h.C;
+  return ok;
+}
+
+__device__ __forceinline__ void store_symbol(uint8_t *dst, uint32_t v,
+                                             uint32_t S, bool aligned) {
+  if (aligned && S == 4) {
+    *reinterpret_cast<uint32_t *>(dst) = v;
+  } else if (aligned && S == 2) {
+    *reinterpret_cast<uint16_t *>(dst) = static_cast<uint16_t>(v);
+  } else {
+    for (uint32_t i = 0; i < S; ++i) dst[i] = static_cast<uint8_t>(v >> (8 * i));
+  }
+}
+
+// Sum of the record sizes of chunks [lo, hi) (hi - lo <= 64).
+__device__ __forceinline__ uint64_t record_bytes(const uint8_t *table,
+                                                 uint32_t lo, uint32_t hi,
+                                                 uint32_t lane) {
+  uint64_t part = 0;
+  for (uint32_t e = lo + lane; e < hi; e += 32) {
+    const uint64_t ntok = ld_le(table + 8ull * e, 4);
+    const uint64_t pay = ld_le(table + 8ull * e + 4, 4);
+    part += (ntok + 7) / 8 + pay;
+  }
+  return warp_sum_u64(part);
+}
+
+__device__ __forceinline__ void decode_chunk(const DecompressArgs &A,
+                                             const Header &h, uint32_t c,
+                                             uint64_t records_at,
+                                             uint32_t *ring, uint32_t rmask,
+                                             uint32_t lane) {
+  const uint8_t *in = A.in;
+  const uint8_t *table = in + kHeaderBytes;
+  const uint8_t *index = table + 8ull * h.nc;
+  const uint32_t j = c / kIndexStride;
+  const uint64_t idxv = ld_le(index + 8ull * j, 8);
+  const uint64_t part = record_bytes(table, j * kIndexStride, c, lane);
+  bool bad = false;
+  if (c == 0) bad = idxv != 0;
+  if (c % kIndexStride == 0 && c > 0) {
+    const uint64_t prev = ld_le(index + 8ull * (j - 1), 8);
+    const uint64_t sb = record_bytes(table, c - kIndexStride, c, lane);
+    bad = bad || prev + sb != idxv;
+  }
+  const uint32_t ntok = static_cast<uint32_t>(ld_le(table + 8ull * c, 4));
+  const uint32_t pay = static_cast<uint32_t>(ld_le(table + 8ull * c + 4, 4));
+  const uint64_t fb = (static_cast<uint64_t>(ntok) + 7) / 8;
+  const uint64_t rec_at = records_at + idxv + part;
+  const uint64_t chunk_at = static_cast<uint64_t>(c) * h.C;
+  const uint32_t k = static_cast<uint32_t>(
+      ((c + 1 < h.nc) ? h.C : h.n - chunk_at) / h.S);
+  bad = bad || idxv > A.in_bytes || rec_at + fb + pay > A.in_bytes ||
+        rec_at + fb + pay < rec_at || ntok > k || (ntok == 0 && k > 0);
+  if (bad) {
+    if (lane == 0) atomicOr(A.err, kErrCorrupt);
+    return;
+  }
+  const uint8_t *flags = in + rec_at;
+  const uint8_t *payload = flags + fb;
+  uint8_t *dst = A.out + chunk_at;
+  const uint32_t S = h.S, offB = h.offB, tsz = 1 + h.offB;
+  const bool aligned = A.out_aligned != 0;
+  const uint32_t lt = lanemask_lt(lane);
+
+  uint32_t pos = 0;       // symbols produced
+  uint64_t pay_used = 0;  // payload bytes consumed
+  for (uint32_t tb = 0; tb < ntok; tb += 32) {
+    const uint32_t t = tb + lane;
+    const bool valid = t < ntok;
+    const bool ism = valid && ((flags[t >> 3] >> (t & 7)) & 1u);
+    const uint32_t mm = __ballot_sync(kFull, ism);
+    const uint32_t vm = __ballot_sync(kFull, valid);
+    const uint32_t nmb = __popc(mm & lt);
+    const uint32_t nlb = __popc(vm & ~mm & lt);
+    const uint64_t my_off = pay_used + S * nlb + tsz * nmb;
+    const uint32_t my_sz = ism ? tsz : (valid ? S : 0u);
+    bool tbad = valid && my_off + my_sz > pay;
+    uint32_t len = valid ? 1u : 0u, off = 0, val = 0;
+    if (valid && !tbad) {
+      if (ism) {
+        len = payload[my_off];
+        off = payload[my_off + 1];
+        if (offB == 2) off |= static_cast<uint32_t>(payload[my_off + 2]) << 8;
+        off += 1;
+      } else {
+        val = static_cast<uint32_t>(ld_le(payload + my_off, S));
+      }
+    }
+    tbad = tbad || (ism && (len == 0 || off > h.W));
+    // inclusive scan of token lengths -> output start of each token
+    uint32_t x = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, x, o);
+      if (lane >= static_cast<uint32_t>(o)) x += y;
+    }
+    const uint32_t group_len = __shfl_sync(kFull, x, 31);
+    const uint32_t start = pos + x - len;
+    tbad = tbad || (ism && off > start);
+    tbad = tbad || pos + group_len > k;
+    if (__any_sync(kFull, tbad)) {
+      if (lane == 0) atomicOr(A.err, kErrCorrupt);
+      return;
+    }
+    const uint32_t end = pos + group_len;
+    if (mm == 0) {
+      // all literals: lane i produces symbol pos + i
+      if (valid) {
+        ring[(pos + lane) & rmask] = val;
+        store_symbol(dst + static_cast<uint64_t>(pos + lane) * S, val, S, aligned);
+      }
+    } else {
+      const uint32_t start_key = valid ? start : kFull;
+      for (uint32_t r0 = pos; r0 < end; r0 += 32) {
+        const uint32_t jp = r0 + lane;
+        const bool active = jp < end;
+        // owning token: the last lane whose start is <= jp
+        uint32_t lo = 0;
+#pragma unroll
+        for (uint32_t step = 16; step > 0; step >>= 1) {
+          const uint32_t s = __shfl_sync(kFull, start_key, lo + step);
+          if (s <= jp) lo += step;
+        }
+        const uint32_t o_ism = __shfl_sync(kFull, ism ? 1u : 0u, lo);
+        const uint32_t o_off = __shfl_sync(kFull, off, lo);
+        const uint32_t o_val = __shfl_sync(kFull, val, lo);
+        uint32_t f = (active && o_ism) ? jp - o_off : jp;
+        // resolve sources inside this round by pointer jumping
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+          const uint32_t src_lane = f >= r0 ? f - r0 : lane;
+          const uint32_t g = __shfl_sync(kFull, f, src_lane);
+          if (f >= r0) f = g;
+        }
+        const uint32_t v_here = __shfl_sync(kFull, o_val, f >= r0 ? f - r0 : lane);
+        const uint32_t v = f >= r0 ? v_here : ring[f & rmask];
+        __syncwarp();
+        if (active) {
+          ring[jp & rmask] = v;
+          store_symbol(dst + static_cast<uint64_t>(jp) * S, v, S, aligned);
+        }
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    pos = end;
+    pay_used += S * __popc(vm & ~mm) + tsz * __popc(mm);
+  }
+  if (pos != k || pay_used != pay) {
+    if (lane == 0) atomicOr(A.err, kErrCorrupt);
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) decompress_kernel(const DecompressArgs A) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warp = threadIdx.x >> 5;
+  const uint32_t wpb = blockDim.x >> 5;
+  uint32_t *ring = reinterpret_cast<uint32_t *>(smem + warp * A.per_warp);
+
+  Header h;
+  const bool ok = read_header(A.in, h);
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  if (!ok) {
+    if (leader) atomicOr(A.err, kErrCorrupt);
+    return;
+  }
+  if (h.n > A.out_cap) {
+    if (leader) atomicOr(A.err, kErrSmall);
+    return;
+  }
+  const uint64_t records_at = kHeaderBytes + 8ull * h.nc +
+                              8ull * ((h.nc + kIndexStride - 1) / kIndexStride);
+  if (records_at > A.in_bytes) {
+    if (leader) atomicOr(A.err, kErrCorrupt);
+    return;
+  }
+  // ring of decoded symbols: a power of two >= W + 32 entries
+  uint32_t ring_n = 64;
+  while (ring_n < h.W + 32) ring_n <<= 1;
+  const uint32_t rmask = ring_n - 1;
+
+  const uint32_t gw = blockIdx.x * wpb + warp;
+  const uint32_t nwarps = gridDim.x * wpb;
+  for (uint32_t c = gw; c < h.nc; c += nwarps)
+    decode_chunk(A, h, c, records_at, ring, rmask, lane);
+  if (leader) *A.out_bytes = h.n;
+}
+
+// Shared bytes per warp: a ring of up to 2048 u32 symbols (W <= 1024).
+constexpr uint32_t kDecodeRingBytes = 2048 * 4;
+
+cudaError_t launch_decompress(DecompressArgs A, int block, cudaStream_t stream) {
+  static std::mutex mu;
+  static int per_sm = 0, sms = 0, cached_block = -1;
+  A.per_warp = kDecodeRingBytes;
+  const size_t smem = static_cast<size_t>(A.per_warp) * (block / 32);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (cached_block != block) {
+      cudaError_t e = cudaFuncSetAttribute(
+          decompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+          static_cast<int>(smem));
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decompress_kernel,
+                                                        block, smem);
+      if (e != cudaSuccess) return e;
+      int dev = 0;
+      e = cudaGetDevice(&dev);
+      if (e != cudaSuccess) return e;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
+      cached_block = block;
+    }
+  }
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // enough warps for the largest stream the input could hold, capped at the
+  // resident limit (the grid cannot depend on the header: it is on the GPU)
+  const uint64_t max_chunks = A.in_bytes / kTableEntry + 1;
+  const uint64_t warps = block / 32;
+  const uint64_t want = (max_chunks + warps - 1) / warps;
+  const uint64_t cap = static_cast<uint64_t>(per_sm) * sms;
+  const unsigned grid = static_cast<unsigned>(want < cap ? want : cap);
+  decompress_kernel<<<grid, block, smem, stream>>>(A);
+  return cudaGetLastError();
+}
+
+}  // namespace glz

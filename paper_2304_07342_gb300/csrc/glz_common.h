@@ -1,0 +1,63 @@
+// glz_common.h -- launch-parameter structs shared by the host side of the
+// C ABI and the kernels (product code only).
+#pragma once
+
+#include <cstdint>
+
+namespace glz {
+
+constexpr uint32_t kHeaderBytes = 32;   // GLZ1 header
+constexpr uint32_t kTableEntry = 8;     // {u32 n_tokens, u32 payload_bytes}
+constexpr uint32_t kIndexStride = 64;   // one u64 index entry per 64 chunks
+constexpr uint32_t kMaxChunk = 32768;   // bytes
+constexpr uint32_t kMaxWindow = 1024;   // symbols
+
+// Sticky device error bits (lz_sync maps them back to lz_status).
+constexpr uint32_t kErrSmall = 1u << 0;
+constexpr uint32_t kErrCorrupt = 1u << 1;
+constexpr uint32_t kErrTimeout = 1u << 2;
+
+// Bounded spins: a device wait that exceeds this many polls gives up and
+// raises kErrTimeout instead of hanging the GPU.
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// Per-warp shared-memory layout of the compressor (byte offsets from the
+// warp's slice; every region 16-byte aligned).
+struct CompressSmem {
+  uint32_t in_off;     // staged chunk, C bytes
+  uint32_t flags_off;  // flag bits of up to k tokens
+  uint32_t pay_off;    // payload staging (worst case); also hash table
+  uint32_t maybe_off;  // one bit per position: a match of >= m may exist
+  uint32_t mbar_off;   // mbarrier for the TMA bulk copy
+  uint32_t per_warp;   // total bytes per warp
+  uint32_t hash_log2;  // hash table entries = 1 << hash_log2 (u16 each)
+};
+
+struct CompressArgs {
+  const uint8_t *in;
+  uint64_t n;
+  uint8_t *out;
+  uint64_t cap;
+  unsigned long long *out_bytes;
+  uint32_t S, C, W, m, M, offB;
+  uint32_t nc;          // chunks
+  uint64_t records_at;  // byte offset of the records region
+  int in_aligned;       // in is 16-byte aligned: TMA bulk staging
+  CompressSmem sm;
+  unsigned long long *status;  // nc look-back words (cleared per call)
+  uint32_t *ticket;            // work counter (cleared per call)
+  uint32_t *err;               // sticky error bits
+};
+
+struct DecompressArgs {
+  const uint8_t *in;
+  uint64_t in_bytes;
+  uint8_t *out;
+  uint64_t out_cap;
+  unsigned long long *out_bytes;
+  uint32_t *err;
+  uint32_t per_warp;  // shared bytes per warp (ring of decoded symbols)
+  int out_aligned;    // out is 16-byte aligned
+};
+
+}  // namespace glz

@@ -1,0 +1,231 @@
+"""Thin Python binding of the C ABI in ``include/lz.h`` (ctypes).
+
+The functions named ``lz_*`` mirror the C entry points one to one and take
+raw device pointers (ints) and a ``cudaStream_t`` handle (int, 0 = legacy
+default stream).  :class:`Codec` adds torch-tensor marshalling on top.  All
+compression work happens in the CUDA kernels of ``liblz.so``; there is no
+CPU path, and every call raises :class:`LzError` if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblz.so")
+
+LZ_OK = 0
+LZ_ERR_INVALID_ARG = 1
+LZ_ERR_BUFFER_TOO_SMALL = 2
+LZ_ERR_CORRUPT = 3
+LZ_ERR_NOMEM = 4
+LZ_ERR_CUDA = 5
+LZ_ERR_TIMEOUT = 6
+
+_NAMES = {0: "LZ_OK", 1: "LZ_ERR_INVALID_ARG", 2: "LZ_ERR_BUFFER_TOO_SMALL",
+          3: "LZ_ERR_CORRUPT", 4: "LZ_ERR_NOMEM", 5: "LZ_ERR_CUDA",
+          6: "LZ_ERR_TIMEOUT"}
+
+# every symbol include/lz.h declares
+EXPORTS = ("lz_create", "lz_destroy", "lz_status_string", "lz_check_params",
+           "lz_compressed_bound", "lz_compress", "lz_decompressed_size",
+           "lz_decompress", "lz_sync")
+
+
+class LzError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        super().__init__(f"{what}: {_NAMES.get(status, status)}")
+        self.status = status
+
+
+class lz_params(ctypes.Structure):
+    _fields_ = [("symbol_bytes", ctypes.c_uint32), ("chunk_bytes", ctypes.c_uint32),
+                ("window", ctypes.c_uint32), ("min_match", ctypes.c_uint32),
+                ("max_match", ctypes.c_uint32)]
+
+
+@dataclass(frozen=True)
+class Params:
+    """S symbol bytes, C chunk bytes, W window (symbols), m min match, M max match."""
+    S: int
+    C: int
+    W: int
+    m: int
+    M: int = 255
+
+    def c(self) -> lz_params:
+        return lz_params(self.S, self.C, self.W, self.m, self.M)
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load ``liblz.so`` (raises LzError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise LzError(LZ_ERR_CUDA, f"CUDA library not built ({path}); run "
+                      "paper_2304_07342_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+    pp = ctypes.POINTER(lz_params)
+    lib.lz_create.argtypes = [ctypes.POINTER(vp), i32]
+    lib.lz_create.restype = i32
+    lib.lz_destroy.argtypes = [vp]
+    lib.lz_destroy.restype = None
+    lib.lz_status_string.argtypes = [i32]
+    lib.lz_status_string.restype = ctypes.c_char_p
+    lib.lz_check_params.argtypes = [pp]
+    lib.lz_check_params.restype = i32
+    lib.lz_compressed_bound.argtypes = [u64, pp]
+    lib.lz_compressed_bound.restype = u64
+    lib.lz_compress.argtypes = [vp, vp, u64, pp, vp, u64, vp, vp]
+    lib.lz_compress.restype = i32
+    lib.lz_decompressed_size.argtypes = [vp, u64, ctypes.POINTER(u64), vp]
+    lib.lz_decompressed_size.restype = i32
+    lib.lz_decompress.argtypes = [vp, vp, u64, vp, u64, vp, vp]
+    lib.lz_decompress.restype = i32
+    lib.lz_sync.argtypes = [vp, vp]
+    lib.lz_sync.restype = i32
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != LZ_OK:
+        raise LzError(status, what)
+
+
+# --- the C entry points, same names -------------------------------------------
+
+def lz_create(device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().lz_create(ctypes.byref(h), device), "lz_create")
+    return h.value
+
+
+def lz_destroy(ctx: int) -> None:
+    load().lz_destroy(ctx)
+
+
+def lz_status_string(status: int) -> str:
+    return load().lz_status_string(status).decode()
+
+
+def lz_check_params(p: Params) -> int:
+    return load().lz_check_params(ctypes.byref(p.c()))
+
+
+def lz_compressed_bound(n_bytes: int, p: Params) -> int:
+    return int(load().lz_compressed_bound(n_bytes, ctypes.byref(p.c())))
+
+
+def lz_compress(ctx: int, d_in: int, n_bytes: int, p: Params, d_out: int,
+                out_cap: int, d_out_bytes: int, stream: int = 0) -> None:
+    _check(load().lz_compress(ctx, d_in, n_bytes, ctypes.byref(p.c()), d_out,
+                              out_cap, d_out_bytes, stream), "lz_compress")
+
+
+def lz_decompressed_size(d_in: int, in_bytes: int, stream: int = 0) -> int:
+    n = ctypes.c_uint64()
+    _check(load().lz_decompressed_size(d_in, in_bytes, ctypes.byref(n), stream),
+           "lz_decompressed_size")
+    return n.value
+
+
+def lz_decompress(ctx: int, d_in: int, in_bytes: int, d_out: int, out_cap: int,
+                  d_out_bytes: int, stream: int = 0) -> None:
+    _check(load().lz_decompress(ctx, d_in, in_bytes, d_out, out_cap,
+                                d_out_bytes, stream), "lz_decompress")
+
+
+def lz_sync(ctx: int, stream: int = 0) -> int:
+    """Return (and clear) the sticky device status; does not raise."""
+    return load().lz_sync(ctx, stream)
+
+
+# --- torch marshalling -----------------------------------------------------------
+
+class Codec:
+    """One context on one device; tensors in, tensors out.
+
+    ``compress``/``decompress`` enqueue on the current torch stream and return
+    the output buffer plus a device int64 holding the produced size;
+    ``*_sync`` variants synchronise, check the sticky status and trim.
+    """
+
+    def __init__(self, device: int = 0):
+        import torch
+        self.torch = torch
+        self.device = device
+        torch.cuda.set_device(device)
+        self.ctx = lz_create(device)
+
+    def close(self):
+        if self.ctx:
+            lz_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self, stream):
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.device)
+        return s.cuda_stream
+
+    @staticmethod
+    def _bytes_of(x):
+        return x.contiguous().view(-1).view(__import__("torch").uint8)
+
+    def compress(self, x, p: Params, out=None, out_bytes=None, stream=None):
+        torch = self.torch
+        xb = self._bytes_of(x)
+        cap = lz_compressed_bound(xb.numel(), p)
+        if cap == 0:
+            raise LzError(LZ_ERR_INVALID_ARG, "lz_compressed_bound")
+        if out is None:
+            out = torch.empty(cap, dtype=torch.uint8, device=xb.device)
+        if out_bytes is None:
+            out_bytes = torch.zeros(1, dtype=torch.int64, device=xb.device)
+        lz_compress(self.ctx, xb.data_ptr(), xb.numel(), p, out.data_ptr(),
+                    out.numel(), out_bytes.data_ptr(), self._stream(stream))
+        return out, out_bytes
+
+    def decompress(self, stream_bytes, n_bytes: int | None = None, out=None,
+                   out_bytes=None, in_bytes: int | None = None, stream=None):
+        torch = self.torch
+        sb = stream_bytes
+        nin = sb.numel() if in_bytes is None else in_bytes
+        if out is None:
+            if n_bytes is None:
+                n_bytes = lz_decompressed_size(sb.data_ptr(), nin, self._stream(stream))
+            out = torch.empty(max(n_bytes, 1), dtype=torch.uint8, device=sb.device)
+        if out_bytes is None:
+            out_bytes = torch.zeros(1, dtype=torch.int64, device=sb.device)
+        lz_decompress(self.ctx, sb.data_ptr(), nin, out.data_ptr(),
+                      out.numel() if n_bytes is None else n_bytes,
+                      out_bytes.data_ptr(), self._stream(stream))
+        return out, out_bytes
+
+    def sync(self, stream=None) -> int:
+        return lz_sync(self.ctx, self._stream(stream))
+
+    def compress_sync(self, x, p: Params, stream=None):
+        out, nb = self.compress(x, p, stream=stream)
+        st = self.sync(stream)
+        if st != LZ_OK:
+            raise LzError(st, "compress (device)")
+        return out[: int(nb.item())]
+
+    def decompress_sync(self, stream_bytes, stream=None):
+        out, nb = self.decompress(stream_bytes, stream=stream)
+        st = self.sync(stream)
+        if st != LZ_OK:
+            raise LzError(st, "decompress (device)")
+        return out[: int(nb.item())]
