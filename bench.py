@@ -1,0 +1,380 @@
+"""Benchmark: chunked multi-byte LZSS compression/decompression on one GB300.
+
+Default workload (one GPU): the large-field configuration -- a 512x512x256
+float32 smooth field (sum of 16 Gaussians + N(0, 1e-4) noise, 256 MiB) and a
+128 Mi-entry int32 sorted-index array (geometric(0.3) gaps, 512 MiB), both
+compressed as 4-byte symbols with chunk 8192 B, window 256, min match 2,
+max match 255.  One step = compress both arrays + decompress both streams
+(the whole path); `value` is compression throughput in input GB/s, and the
+line also carries decompression GB/s and the compression ratio.
+
+Timing: W untimed warm-up steps, then K steps bracketed by a barrier and
+torch.cuda.synchronize(), CUDA events on the launching stream; inputs (768
+MiB) are larger than L2 (126 MB), so no extra flush is needed.  SM clocks
+are sampled with nvidia-smi during the timed region.  Under torchrun each
+rank compresses its own shard (independent data, weak scaling); there is no
+data-path collective.
+
+`--impl reference` times the CPU oracle (the plain definition) on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("compress/decompress input GB/s + ratio vs HBM roofline; "
+          "batched/served GB/s, p50/p99 latency")
+
+# workload name -> list of (label, generator, params (S, C, W, m, M))
+def _workloads():
+    from paper_2304_07342_gb300 import synth
+    return {
+        "field+indices": [
+            ("float32 field 512x512x256", lambda r: synth.gaussian_field(seed=r),
+             (4, 8192, 256, 2, 255)),
+            ("int32 sorted indices 128Mi", lambda r: synth.sorted_indices(128 << 20, seed=r),
+             (4, 8192, 256, 2, 255)),
+        ],
+        "quant-small": [
+            ("uint16 quant codes 1MiB", lambda r: synth.workload_small(seed=r),
+             (2, 4096, 128, 3, 255)),
+        ],
+        # small cases for profiling: same kernels, a few GB at most
+        "field-32MiB": [
+            ("float32 field 64x512x256", lambda r: synth.gaussian_field((64, 512, 256), seed=r),
+             (4, 8192, 256, 2, 255)),
+        ],
+        "markov16-64MiB": [
+            ("uint16 markov codes 32Mi", lambda r: synth.markov_codes(32 << 20, seed=r).astype(np.uint16),
+             (2, 4096, 128, 3, 255)),
+        ],
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(
+                    ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                     "--format=csv,noheader,nounits"],
+                    capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([f.strip() for f in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            for name, v in zip(names, s[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2304_07342_gb300 import build, lz
+    rank, world, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    codec = lz.Codec(local)
+    stream = torch.cuda.current_stream()
+
+    items = []
+    for label, gen, P in _workloads()[args.workload]:
+        x = gen(args.seed + rank)  # each rank: its own shard of independent data
+        xb = np.ascontiguousarray(x).view(np.uint8).reshape(-1)
+        p = lz.Params(*P)
+        d_in = torch.from_numpy(xb).to(f"cuda:{local}")
+        cap = lz.lz_compressed_bound(xb.size, p)
+        d_out = torch.empty(cap, dtype=torch.uint8, device=d_in.device)
+        d_nb = torch.zeros(1, dtype=torch.int64, device=d_in.device)
+        d_dec = torch.empty_like(d_in)
+        d_db = torch.zeros(1, dtype=torch.int64, device=d_in.device)
+        items.append(dict(label=label, host=xb, p=p, d_in=d_in, d_out=d_out, d_nb=d_nb,
+                          d_dec=d_dec, d_db=d_db, cap=cap))
+
+    def compress_all():
+        for it in items:
+            lz.lz_compress(codec.ctx, it["d_in"].data_ptr(), it["d_in"].numel(), it["p"],
+                           it["d_out"].data_ptr(), it["cap"], it["d_nb"].data_ptr(),
+                           stream.cuda_stream)
+
+    def decompress_all():
+        for it in items:
+            lz.lz_decompress(codec.ctx, it["d_out"].data_ptr(), it["size"],
+                             it["d_dec"].data_ptr(), it["d_dec"].numel(),
+                             it["d_db"].data_ptr(), stream.cuda_stream)
+
+    # first pass: sizes and a correctness check of the round trip
+    compress_all()
+    if codec.sync() != lz.LZ_OK:
+        raise RuntimeError("compress failed on the device")
+    for it in items:
+        it["size"] = int(it["d_nb"].item())
+    decompress_all()
+    if codec.sync() != lz.LZ_OK:
+        raise RuntimeError("decompress failed on the device")
+    for it in items:
+        if not torch.equal(it["d_dec"], it["d_in"]):
+            raise RuntimeError(f"round trip mismatch: {it['label']}")
+
+    n_in = sum(it["d_in"].numel() for it in items)
+    n_out = sum(it["size"] for it in items)
+
+    for _ in range(args.warmup):
+        compress_all()
+        decompress_all()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # per-kernel events for the roofline: first item's compress launch
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for s in range(args.steps):
+            a, b, c = ev[s]
+            a.record(stream)
+            ka, kb = kev[s]
+            for i, it in enumerate(items):
+                if i == 0:
+                    ka.record(stream)
+                lz.lz_compress(codec.ctx, it["d_in"].data_ptr(), it["d_in"].numel(), it["p"],
+                               it["d_out"].data_ptr(), it["cap"], it["d_nb"].data_ptr(),
+                               stream.cuda_stream)
+                if i == 0:
+                    kb.record(stream)
+            b.record(stream)
+            decompress_all()
+            c.record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    if codec.sync() != lz.LZ_OK:
+        raise RuntimeError("device error during the timed steps")
+
+    total_ms = t0.elapsed_time(t1)
+    comp_ms = sum(a.elapsed_time(b) for a, b, _ in ev) / args.steps
+    dec_ms = sum(b.elapsed_time(c) for _, b, c in ev) / args.steps
+    k_ms = sum(a.elapsed_time(b) for a, b in kev) / args.steps
+    if world > 1:
+        t = torch.tensor([total_ms, comp_ms, dec_ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, comp_ms, dec_ms = t.tolist()
+
+    # end to end through the public API with host buffers: pinned input ->
+    # device, compress, compressed stream -> pinned host, every step
+    e2e = _e2e(codec, items, stream, args)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return None
+    peaks = _peaks() or {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    it0 = items[0]
+    k_bytes = it0["d_in"].numel() + it0["size"]  # read input + write stream
+    achieved = k_bytes / (k_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": round(n_in * world / (comp_ms * 1e-3) / 1e9, 3),
+        "unit": "GB/s (input bytes compressed per second)",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8/u32 symbols (integer/byte path, lossless)",
+        "data": "synthetic (seeded generators shaped like the paper's workloads)",
+        "config": {"workload": args.workload,
+                   "items": [dict(label=it["label"], bytes=int(it["d_in"].numel()),
+                                  params=dict(zip("SCWmM", [it["p"].S, it["p"].C, it["p"].W,
+                                                             it["p"].m, it["p"].M])))
+                             for it in items],
+                   "l2": "inputs larger than L2, no flush", "parallelism": f"replicas{world}"},
+        "compress_gbs": round(n_in / (comp_ms * 1e-3) / 1e9, 3),
+        "decompress_gbs": round(n_in / (dec_ms * 1e-3) / 1e9, 3),
+        "ratio": round(n_in / n_out, 4),
+        "compress_ms": round(comp_ms, 4),
+        "decompress_ms": round(dec_ms, 4),
+        "roofline": {"kernel": "compress_kernel (" + it0["label"] + ")",
+                     "bound": "hbm", "achieved": round(achieved, 2),
+                     "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 5),
+                     "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+        "e2e": e2e,
+        "gpu_launches": args.steps * len(items) * 2,
+        "clocks": clk.summary(),
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(args, hosts=[it["host"] for it in items])
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
+def _e2e(codec, items, stream, args):
+    import torch
+
+    from paper_2304_07342_gb300 import lz
+    pinned_in = [torch.from_numpy(it["host"]).pin_memory() for it in items]
+    pinned_out = [torch.empty(it["cap"], dtype=torch.uint8).pin_memory() for it in items]
+    steps = max(1, min(args.steps, 5))
+
+    def one():
+        for it, hi, ho in zip(items, pinned_in, pinned_out):
+            it["d_in"].copy_(hi, non_blocking=True)
+            lz.lz_compress(codec.ctx, it["d_in"].data_ptr(), it["d_in"].numel(), it["p"],
+                           it["d_out"].data_ptr(), it["cap"], it["d_nb"].data_ptr(),
+                           stream.cuda_stream)
+            ho[: it["size"]].copy_(it["d_out"][: it["size"]], non_blocking=True)
+
+    one()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        one()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    n_in = sum(it["d_in"].numel() for it in items)
+    return {"value": round(n_in / (ms * 1e-3) / 1e9, 3), "unit": "GB/s",
+            "h2d_bytes_per_step": int(n_in),
+            "d2h_bytes_per_step": int(sum(it["size"] for it in items)),
+            "note": "stream size known from the warm-up pass; D2H copies exactly that many bytes"}
+
+
+def _cpu_baseline(args, budget_s: float = 15.0, hosts=None):
+    """The oracle as it stands, one host thread, on a bounded sample (leading
+    whole chunks of each item) of the same workload."""
+    import oracle
+    oracle.build()
+    t_total, n_total, desc = 0.0, 0, []
+    per_item = budget_s / len(_workloads()[args.workload])
+    for i, (label, gen, P) in enumerate(_workloads()[args.workload]):
+        x = hosts[i] if hosts is not None else gen(args.seed)
+        x = np.ascontiguousarray(x).view(np.uint8).reshape(-1)
+        p = oracle.Params(*P)
+        n = min(x.size, 64 * P[1])
+        t = time.perf_counter()
+        oracle.compress(x[:n], p)
+        dt = time.perf_counter() - t
+        # grow the sample until the budget is used (rate is ~constant per chunk)
+        n2 = int(min(x.size, max(n, n * per_item / max(dt, 1e-6) * 0.8)))
+        n2 -= n2 % P[1]
+        if n2 > n:
+            t = time.perf_counter()
+            oracle.compress(x[:n2], p)
+            dt = time.perf_counter() - t
+            n = n2
+        t_total += dt
+        n_total += n
+        desc.append(f"{label}: first {n} bytes")
+    return {"value": round(n_total / t_total / 1e9, 6), "unit": "GB/s", "cores": 1,
+            "kind": "oracle", "sample": "; ".join(desc)}
+
+
+def run_reference(args):
+    rank, world, local = _dist()
+    if rank != 0:
+        return None
+    cb = _cpu_baseline(args, budget_s=max(5.0, 60.0 / max(1, args.steps + args.warmup)))
+    return {
+        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"],
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8/u32 symbols", "data": "synthetic",
+        "config": {"workload": args.workload},
+        "cpu_baseline": cb,
+        "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="field+indices")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    line = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -67,7 +67,9 @@ typedef enum lz_status {
   LZ_ERR_CORRUPT = 3,          /* input is not a well-formed GLZ1 stream  */
   LZ_ERR_NOMEM = 4,            /* context scratch allocation failed       */
   LZ_ERR_CUDA = 5,             /* CUDA runtime error (launch, copy, ...)  */
-  LZ_ERR_TIMEOUT = 6           /* a bounded device-side wait gave up      */
+  LZ_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up      */
+  LZ_ERR_INTERNAL = 7          /* a device-side consistency check failed
+                                  (a bug in this library; output invalid) */
 } lz_status;
 
 typedef struct lz_ctx lz_ctx;
@@ -128,7 +130,7 @@ lz_status lz_decompress(lz_ctx *ctx, const void *d_in, uint64_t in_bytes,
 
 /* Synchronise `stream`, then return and clear the context's sticky device
  * error (LZ_OK if none).  When several errors occurred the most severe is
- * returned: TIMEOUT, then CORRUPT, then BUFFER_TOO_SMALL. */
+ * returned: INTERNAL, TIMEOUT, CORRUPT, then BUFFER_TOO_SMALL. */
 lz_status lz_sync(lz_ctx *ctx, lz_stream_t stream);
 
 #ifdef __cplusplus

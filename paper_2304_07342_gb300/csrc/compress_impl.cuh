@@ -5,19 +5,19 @@
 // III (deflate, 3.3.4).  Here all of it is one persistent kernel; each warp
 // takes the next chunk from a work counter and
 //   1. stages the chunk into its shared-memory slice (1-D TMA bulk copy);
-//   2. marks the positions where a match of >= m symbols can exist, with a
-//      last-occurrence hash table over the first min(m, 8/S) symbols
-//      (__match_any_sync resolves collisions inside a 32-position slab);
-//      the filter is conservative, so skipping unmarked positions as
-//      literals leaves the greedy parse unchanged;
-//   3. walks the greedy parse (section 2.2 steps 1-6): at a marked position
-//      the lanes hold the candidate offsets d = lane+1+32j and advance the
-//      match one symbol per step, dropping offsets whose symbol differs or
-//      that reached d <= length (length <= offset, section 3.3.2), until no
-//      candidate survives; the longest length wins, then the smallest
-//      offset (warp min).  Tokens are appended to a staging record in
-//      shared memory -- the running byte count is the local (first) pass of
-//      the two-pass prefix sum (section 3.2.2);
+//   2. links every position to the last earlier position with the same
+//      hash of its first min(m, 8/S) symbols (hash chains; __match_any_sync
+//      links positions of one 32-position slab) and marks the positions
+//      whose chain reaches into the window -- only those can start a match
+//      of >= m symbols;
+//   3. walks the greedy parse (section 2.2 steps 1-6): the next 32 marked
+//      positions are evaluated in parallel, one lane each, by walking their
+//      chains nearest-first and extending every candidate exactly (length
+//      <= offset, section 3.3.2); the parse through the batch is found by a
+//      short chase over lanes, then warp scans give each token its index
+//      and payload offset (the local, first pass of the two-pass prefix sum
+//      of section 3.2.2) and the lanes write the tokens in parallel into a
+//      staging record in shared memory;
 //   4. obtains its record's global offset from a decoupled look-back over
 //      the chunks before it (the second pass) -- bounded spins, no extra
 //      kernel, no per-symbol data in HBM;
@@ -46,26 +46,47 @@ struct SymType<4> {
   using T = uint32_t;
 };
 
-// Step 2: one bit per position, set where a match of >= m symbols may
-// start.  A position p can only have such a match if the same first
-// g = min(m, 8/S) symbols occur at some q in [p-W, p-1]; the table keeps,
-// per hash of those g symbols, the last position inserted, so "last
-// occurrence older than W" proves there is none.
+constexpr uint16_t kNoPos = 0xFFFF;  // chunk positions are < 32768
+
+// Chain links: distance from a position to the previous one with the same
+// key hash, 0 if there is none within the window.  One byte per position
+// while W <= 255, two bytes beyond.
+struct Links {
+  uint8_t *base;
+  bool wide;
+  __device__ __forceinline__ uint32_t get(uint32_t p) const {
+    return wide ? reinterpret_cast<const uint16_t *>(base)[p] : base[p];
+  }
+  __device__ __forceinline__ void set(uint32_t p, uint32_t d) const {
+    if (wide)
+      reinterpret_cast<uint16_t *>(base)[p] = static_cast<uint16_t>(d);
+    else
+      base[p] = static_cast<uint8_t>(d);
+  }
+};
+
+// Step 2: hash chains.  For every position p with room for m symbols, the
+// key is its first g = min(m, 8/S) symbols; the link of p is the distance to
+// the last earlier position with the same key hash when that lies within
+// the window, and bit p of `maybe` is set when there is such a link.  A
+// match of >= m symbols at p from offset d needs p - d to carry the same
+// key, so every such offset is on p's chain, and an unmarked p has none:
+// skipping unmarked positions as literals leaves the greedy parse
+// unchanged.  The table holds the last position per hash;
+// __match_any_sync links the positions of one 32-position slab that share a
+// hash.
 template <int S>
-__device__ __forceinline__ void mark_candidates(const typename SymType<S>::T *sym,
-                                                uint32_t k, const CompressArgs &A,
-                                                uint16_t *table, uint32_t *maybe,
-                                                uint32_t lane) {
+__device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
+                                             uint32_t k, const CompressArgs &A,
+                                             uint16_t *table, uint32_t *maybe,
+                                             const Links &links, uint32_t lane) {
   const uint32_t H = 1u << A.sm.hash_log2;
-  // "last position" = p - (W + 1) for every p: never within the window
-  const uint32_t init16 = static_cast<uint16_t>(0u - A.W - 1u);
-  const uint32_t init32 = init16 | (init16 << 16);
   uint32_t *t32 = reinterpret_cast<uint32_t *>(table);
-  for (uint32_t i = lane; i < H / 2; i += 32) t32[i] = init32;
+  for (uint32_t i = lane; i < H / 2; i += 32) t32[i] = 0xFFFFFFFFu;
   __syncwarp();
 
   const uint32_t g = min(A.m, 8u / S);
-  const uint32_t shift = 64u - A.sm.hash_log2;
+  const uint32_t tshift = 64u - A.sm.hash_log2;
   const uint32_t lt = lanemask_lt(lane);
   const uint32_t nslab = (k + 31) / 32;
   for (uint32_t s = 0; s < nslab; ++s) {
@@ -77,18 +98,17 @@ __device__ __forceinline__ void mark_candidates(const typename SymType<S>::T *sy
       for (uint32_t i = 0; i < 8u / S; ++i)
         if (i < g) key |= static_cast<uint64_t>(sym[p + i]) << (8 * S * i);
     }
-    const uint32_t h =
-        static_cast<uint32_t>((key * 0x9E3779B97F4A7C15ull) >> shift);
+    const uint32_t h = static_cast<uint32_t>((key * 0x9E3779B97F4A7C15ull) >> tshift);
     const uint32_t grp = __match_any_sync(kFull, ok ? h : (0x10000u + lane));
     const uint32_t lower = grp & lt;
-    uint32_t dist;
-    if (lower)
-      dist = lane - (31u - __clz(lower));  // nearest earlier lane, same hash
-    else
-      dist = static_cast<uint16_t>(p - table[h]);
+    const uint32_t q = lower ? s * 32 + (31u - __clz(lower)) : table[h];
+    const uint32_t dist = (ok && q != kNoPos && p - q <= A.W) ? p - q : 0u;
     __syncwarp();
-    if (ok && (grp >> lane) == 1u) table[h] = static_cast<uint16_t>(p);
-    const uint32_t bits = __ballot_sync(kFull, ok && dist <= A.W);
+    if (ok) {
+      links.set(p, dist);
+      if ((grp >> lane) == 1u) table[h] = static_cast<uint16_t>(p);
+    }
+    const uint32_t bits = __ballot_sync(kFull, dist != 0);
     if (lane == 0) maybe[s] = bits;
     __syncwarp();
   }
@@ -99,74 +119,272 @@ __device__ __forceinline__ void warp_copy_bytes(uint8_t *dst, const uint8_t *src
   for (uint32_t i = lane; i < nbytes; i += 32) dst[i] = src[i];
 }
 
+// Length of the match at p from offset d (d >= 1), at most `cap` symbols.
+template <int S>
+__device__ __forceinline__ uint32_t extend(const typename SymType<S>::T *sym,
+                                           uint32_t p, uint32_t d, uint32_t cap) {
+  uint32_t l = 0;
+  while (l < cap && sym[p + l] == sym[p - d + l]) ++l;
+  return l;
+}
+
+// Per-lane work caps of the chain evaluation; a position that needs more
+// (long repetitive runs) is left to the exact window walk below.
+constexpr uint32_t kChainHops = 48;
+constexpr uint32_t kChainWork = 384;
+
+// Exact longest match at position q (one lane): walk q's chain, nearest
+// offset first, extending every offset d >= m that could still beat the
+// best; a strictly longer match replaces the best, so ties keep the nearest.
+// Returns false when the work cap stopped the walk with candidates left.
+template <int S>
+__device__ __forceinline__ bool chain_match(const typename SymType<S>::T *sym,
+                                            uint32_t k, const CompressArgs &A,
+                                            const Links &links, uint32_t q,
+                                            uint32_t &best, uint32_t &bd) {
+  const uint32_t lim = min(A.M, k - q);
+  best = 0;
+  bd = 0;
+  uint32_t d = links.get(q), hops = 0, work = 0;
+  while (d != 0 && d <= A.W) {
+    if (best == lim) return true;
+    if (hops >= kChainHops || work >= kChainWork) return false;
+    if (d >= A.m) {
+      const uint32_t cap = min(lim, d);
+      if (cap > best) {
+        const uint32_t l = extend<S>(sym, q, d, cap);
+        work += l + 1;
+        if (l > best) {
+          best = l;
+          bd = d;
+        }
+      }
+    }
+    ++hops;
+    const uint32_t step = links.get(q - d);
+    if (step == 0) break;
+    d += step;
+  }
+  return true;
+}
+
+// Exact longest match at p by the whole warp (fallback for positions whose
+// chain exceeded the work cap): lanes hold the offsets d = lane + 1 + 32 j
+// and advance the match one symbol per step, dropping offsets whose symbol
+// differs or that reached d <= length (length <= offset), until none is
+// left; the longest survives, the smallest offset breaks ties (warp min).
+template <int S, int NJ>
+__device__ __forceinline__ void window_match(const typename SymType<S>::T *sym,
+                                             uint32_t k, const CompressArgs &A,
+                                             uint32_t p, uint32_t lane,
+                                             uint32_t &L_out, uint32_t &d_out) {
+  using Sym = typename SymType<S>::T;
+  const uint32_t cap = min(A.M, k - p);
+  const uint32_t dlim = min(A.W, p);
+  uint32_t alive = 0;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j)
+    if (lane + 1 + 32 * j <= dlim) alive |= 1u << j;
+  uint32_t L = 0;
+  while (L < cap) {
+    const Sym c = sym[p + L];
+    uint32_t eq = 0;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const int idx = static_cast<int>(p + L) - static_cast<int>(lane + 1 + 32 * j);
+      eq |= static_cast<uint32_t>(sym[idx < 0 ? 0 : idx] == c) << j;
+    }
+    const uint32_t jmin = (L > lane) ? ((L - lane - 1) >> 5) + 1 : 0;
+    const uint32_t capm = jmin >= 32 ? 0u : (kFull << jmin);
+    const uint32_t nxt = alive & eq & capm;
+    if (!__any_sync(kFull, nxt != 0)) break;
+    alive = nxt;
+    ++L;
+  }
+  const uint32_t mine = alive ? lane + 1 + 32 * (__ffs(alive) - 1) : kFull;
+  L_out = L;
+  d_out = L ? __reduce_min_sync(kFull, mine) : 0;
+}
+
+// Index of the (n+1)-th set bit of `bits` (n < popc(bits)): the smallest b
+// with more than n set bits in bits[0..b].
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t bits, uint32_t n) {
+  uint32_t lo = 0;
+#pragma unroll
+  for (uint32_t step = 16; step > 0; step >>= 1) {
+    const uint32_t t = lo + step - 1;  // candidate: is the answer above t?
+    const uint32_t upto = t >= 31 ? kFull : ((2u << t) - 1u);
+    if (static_cast<uint32_t>(__popc(bits & upto)) <= n) lo += step;
+  }
+  return lo;
+}
+
+// Number of lanes whose (ascending) value v is below x.
+__device__ __forceinline__ uint32_t count_below(uint32_t v, uint32_t x) {
+  uint32_t lo = 0;
+#pragma unroll
+  for (uint32_t step = 16; step > 0; step >>= 1) {
+    const uint32_t y = __shfl_sync(kFull, v, lo + step - 1);
+    if (y < x) lo += step;
+  }
+  const uint32_t top = __shfl_sync(kFull, v, 31);  // every lane takes part
+  if (lo == 31 && top < x) lo = 32;
+  return lo;
+}
+
+// First marked position >= p (k if none).
+__device__ __forceinline__ uint32_t next_marked(const uint32_t *maybe, uint32_t p,
+                                                uint32_t k) {
+  if (p >= k) return k;
+  const uint32_t nw = (k + 31) / 32;
+  uint32_t w = p >> 5;
+  uint32_t bits = maybe[w] & (kFull << (p & 31));
+  while (!bits && ++w < nw) bits = maybe[w];
+  return bits ? min(k, (w << 5) + __ffs(bits) - 1) : k;
+}
+
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x, uint32_t lane,
+                                                   uint32_t &total) {
+  uint32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= static_cast<uint32_t>(o)) incl += y;
+  }
+  total = __shfl_sync(kFull, incl, 31);
+  return incl - x;
+}
+
 // Step 3: greedy parse of one chunk into (flags, payload) staging.
+//
+// The marked positions are taken 32 at a time: lane i evaluates the i-th
+// next marked position with chain_match (exact).  The parse through the
+// batch is then a chain over lanes: from lane i (coding position q_i) it
+// moves to the first marked position at or after q_i + len (pointer of
+// len >= m) or q_i + 1 (literal); the unmarked positions in between are
+// literals and marked positions jumped over are covered.  A short serial
+// chase marks the visited lanes; two warp scans give every visited lane its
+// token index and payload offset, and the lanes write their tokens and
+// literal runs in parallel.
 template <int S, int NJ>
 __device__ __forceinline__ void greedy_walk(const typename SymType<S>::T *sym,
                                             uint32_t k, const CompressArgs &A,
-                                            const uint32_t *maybe, uint8_t *flags,
+                                            const uint32_t *maybe,
+                                            const Links &links, uint8_t *flags,
                                             uint8_t *pay, uint32_t lane,
-                                            uint32_t &ntok_out, uint32_t &pay_out) {
-  using Sym = typename SymType<S>::T;
+                                            uint32_t &ntok_out, uint32_t &pay_out,
+                                            bool &sane) {
   const uint8_t *in_bytes = reinterpret_cast<const uint8_t *>(sym);
+  uint32_t *flag_words = reinterpret_cast<uint32_t *>(flags);
+  const uint32_t pay_cap = A.sm.pay_bytes;
+  sane = true;
   const uint32_t nw = (k + 31) / 32;
+  const uint32_t tsz_match = 1 + A.offB;
   uint32_t p = 0, ntok = 0, pb = 0;
   while (p < k) {
-    // next marked position at or after p
-    uint32_t w = p >> 5;
-    uint32_t bits = maybe[w] & (kFull << (p & 31));
-    while (!bits && ++w < nw) bits = maybe[w];
-    const uint32_t q = bits ? min(k, (w << 5) + __ffs(bits) - 1) : k;
-    if (q > p) {  // run of literals
-      const uint32_t nb = (q - p) * S;
+    const uint32_t q0 = next_marked(maybe, p, k);
+    if (q0 > p) {  // run of literals
+      const uint32_t nb = (q0 - p) * S;
+      if (pb + nb > pay_cap) {  // cannot happen for a correct parse
+        sane = false;
+        break;
+      }
       warp_copy_bytes(pay + pb, in_bytes + p * S, nb, lane);
       pb += nb;
-      ntok += q - p;
-      p = q;
+      ntok += q0 - p;
+      p = q0;
       __syncwarp();
-      continue;
+      if (p >= k) break;
     }
-    // longest match at p over offsets d = lane + 1 + 32 j <= min(W, p)
-    const uint32_t cap = min(A.M, k - p);
-    const uint32_t dlim = min(A.W, p);
-    uint32_t alive = 0;
-#pragma unroll
-    for (int j = 0; j < NJ; ++j)
-      if (lane + 1 + 32 * j <= dlim) alive |= 1u << j;
-    uint32_t L = 0;
-    while (L < cap) {
-      const Sym c = sym[p + L];
-      uint32_t eq = 0;
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const int idx = static_cast<int>(p + L) - static_cast<int>(lane + 1 + 32 * j);
-        eq |= static_cast<uint32_t>(sym[idx < 0 ? 0 : idx] == c) << j;
+    // batch: lane i <- i-th marked position >= p
+    uint32_t mypos = k, seen = 0, w = p >> 5;
+    uint32_t bits = maybe[w] & (kFull << (p & 31));
+    while (true) {
+      const uint32_t cnt = __popc(bits);
+      if (lane >= seen && lane < seen + cnt) mypos = (w << 5) + nth_set_bit(bits, lane - seen);
+      seen += cnt;
+      if (seen >= 32 || ++w >= nw) break;
+      bits = maybe[w];
+    }
+    const uint32_t nvalid = min(seen, 32u);
+    const bool valid = lane < nvalid;
+    uint32_t L = 0, bd = 0;
+    bool resolved = true;
+    if (valid) resolved = chain_match<S>(sym, k, A, links, mypos, L, bd);
+    const uint32_t unres = __ballot_sync(kFull, !resolved);
+    uint32_t nxt = valid ? mypos + (L >= A.m ? L : 1u) : k;
+    uint32_t succ = count_below(mypos, nxt);
+    if (!valid) succ = 32;
+    // serial chase over the visited lanes (exact fallback where needed)
+    uint32_t visited = 0, v = 0;
+    while (v < nvalid) {
+      visited |= 1u << v;
+      if ((unres >> v) & 1u) {
+        uint32_t tl, td;
+        const uint32_t pos_v = __shfl_sync(kFull, mypos, v);
+        window_match<S, NJ>(sym, k, A, pos_v, lane, tl, td);
+        const uint32_t nv = pos_v + (tl >= A.m ? tl : 1u);
+        const uint32_t sv = count_below(mypos, nv);
+        if (lane == v) {
+          L = tl;
+          bd = td;
+          nxt = nv;
+          succ = sv;
+        }
       }
-      // offsets d <= L would read the look-ahead itself: drop them
-      const uint32_t jmin = (L > lane) ? ((L - lane - 1) >> 5) + 1 : 0;
-      const uint32_t capm = jmin >= 32 ? 0u : (kFull << jmin);
-      const uint32_t nxt = alive & eq & capm;
-      if (!__any_sync(kFull, nxt != 0)) break;
-      alive = nxt;
-      ++L;
+      v = __shfl_sync(kFull, succ, v);
     }
-    if (L >= A.m) {
-      const uint32_t mine = alive ? lane + 1 + 32 * (__ffs(alive) - 1) : kFull;
-      const uint32_t d = __reduce_min_sync(kFull, mine);
-      if (lane == 0) {
-        flags[ntok >> 3] |= static_cast<uint8_t>(1u << (ntok & 7));
-        pay[pb] = static_cast<uint8_t>(L);
-        pay[pb + 1] = static_cast<uint8_t>((d - 1) & 0xFF);
-        if (A.offB == 2) pay[pb + 2] = static_cast<uint8_t>((d - 1) >> 8);
-      }
-      pb += 1 + A.offB;
-      p += L;
-    } else {
-      if (lane < S) pay[pb + lane] = in_bytes[p * S + lane];
-      pb += S;
-      p += 1;
+    const uint32_t lastv = 31u - __clz(visited);
+    const uint32_t nxt_last = __shfl_sync(kFull, nxt, lastv);
+    const uint32_t after = next_marked(maybe, nxt_last, k);
+    const bool isv = (visited >> lane) & 1u;
+    const uint32_t succ_pos = __shfl_sync(kFull, mypos, succ < 32 ? succ : lane);
+    const uint32_t run_end = (lane == lastv) ? after : succ_pos;
+    const uint32_t run = isv ? run_end - nxt : 0u;
+    const bool is_match = isv && L >= A.m;
+    const uint32_t tsz = is_match ? tsz_match : S;
+    uint32_t tot_t, tot_b;
+    const uint32_t t_off = warp_excl_scan(isv ? 1u + run : 0u, lane, tot_t);
+    const uint32_t b_off = warp_excl_scan(isv ? tsz + run * S : 0u, lane, tot_b);
+    // consistency guard: the batch must stay inside the chunk and the
+    // staging area (always true for a correct parse)
+    if (pb + tot_b > pay_cap || ntok + tot_t > k || after > k || nxt_last > k) {
+      sane = false;
+      break;
     }
-    ++ntok;
+    if (is_match) {
+      const uint32_t t = ntok + t_off;
+      atomicOr(&flag_words[t >> 5], 1u << (t & 31));
+      uint8_t *o = pay + pb + b_off;
+      o[0] = static_cast<uint8_t>(L);
+      o[1] = static_cast<uint8_t>((bd - 1) & 0xFF);
+      if (A.offB == 2) o[2] = static_cast<uint8_t>((bd - 1) >> 8);
+    } else if (isv) {
+      uint8_t *o = pay + pb + b_off;
+      const uint8_t *src = in_bytes + mypos * S;
+#pragma unroll
+      for (int i = 0; i < S; ++i) o[i] = src[i];
+    }
+    // literal runs: short ones by their lane, long ones by the warp
+    const uint32_t rb = run * S;
+    if (isv && rb > 0 && rb <= 32) {
+      uint8_t *o = pay + pb + b_off + tsz;
+      const uint8_t *src = in_bytes + nxt * S;
+      for (uint32_t i = 0; i < rb; ++i) o[i] = src[i];
+    }
+    uint32_t longs = __ballot_sync(kFull, isv && rb > 32);
+    while (longs) {
+      const uint32_t i = __ffs(longs) - 1;
+      longs &= longs - 1;
+      const uint32_t o = __shfl_sync(kFull, pb + b_off + tsz, i);
+      const uint32_t src = __shfl_sync(kFull, nxt * S, i);
+      const uint32_t nb = __shfl_sync(kFull, rb, i);
+      warp_copy_bytes(pay + o, in_bytes + src, nb, lane);
+    }
     __syncwarp();
+    ntok += tot_t;
+    pb += tot_b;
+    p = after;
   }
   ntok_out = ntok;
   pay_out = pb;
@@ -189,7 +407,7 @@ __device__ __forceinline__ uint64_t chunk_lookback(unsigned long long *status,
   if (lane == 0) st_relaxed_u64(&status[c], kAgg | agg);
   uint64_t excl = 0;
   int64_t base = static_cast<int64_t>(c) - 1;
-  uint32_t spins = 0;
+  uint32_t spins = 0, nap = 32;
   while (true) {
     const int64_t idx = base - static_cast<int64_t>(lane);
     const unsigned long long v = idx >= 0 ? ld_relaxed_u64(&status[idx]) : kPrefix;
@@ -203,7 +421,8 @@ __device__ __forceinline__ uint64_t chunk_lookback(unsigned long long *status,
         if (lane == 0) atomicOr(err, kErrTimeout);
         break;
       }
-      __nanosleep(20);
+      __nanosleep(nap);
+      nap = min(nap * 2, 1024u);
       continue;
     }
     excl += warp_sum_u64(lane <= limit ? (v & kVal) : 0ull);
@@ -226,6 +445,7 @@ __global__ void __launch_bounds__(256) compress_kernel(const CompressArgs A) {
   uint8_t *flags = ws + A.sm.flags_off;
   uint8_t *pay = ws + A.sm.pay_off;
   uint32_t *maybe = reinterpret_cast<uint32_t *>(ws + A.sm.maybe_off);
+  const Links links{ws + A.sm.prev_off, A.W > 255};
   uint64_t *bar = reinterpret_cast<uint64_t *>(ws + A.sm.mbar_off);
   const Sym *sym = reinterpret_cast<const Sym *>(inb);
 
@@ -285,14 +505,16 @@ __global__ void __launch_bounds__(256) compress_kernel(const CompressArgs A) {
     __syncwarp();
 
     // 2. candidate filter (hash table lives in the payload staging area)
-    mark_candidates<S>(sym, k, A, reinterpret_cast<uint16_t *>(pay), maybe, lane);
-    const uint32_t fbytes_max = (k + 7) / 8;
-    for (uint32_t i = lane; i < fbytes_max; i += 32) flags[i] = 0;
+    build_chains<S>(sym, k, A, reinterpret_cast<uint16_t *>(pay), maybe, links, lane);
+    const uint32_t fwords = (k + 31) / 32;
+    for (uint32_t i = lane; i < fwords; i += 32) reinterpret_cast<uint32_t *>(flags)[i] = 0;
     __syncwarp();
 
     // 3. greedy parse + local offsets
     uint32_t ntok, pb;
-    greedy_walk<S, NJ>(sym, k, A, maybe, flags, pay, lane, ntok, pb);
+    bool sane;
+    greedy_walk<S, NJ>(sym, k, A, maybe, links, flags, pay, lane, ntok, pb, sane);
+    if (!sane && lane == 0) atomicOr(A.err, kErrInternal);
     const uint32_t fb = (ntok + 7) / 8;
     const uint64_t rec = static_cast<uint64_t>(fb) + pb;
 
@@ -312,7 +534,7 @@ __global__ void __launch_bounds__(256) compress_kernel(const CompressArgs A) {
       st_le_bytes(idx, excl, 8, lane);
     }
     const uint64_t dst = A.records_at + excl;
-    if (ok && staged) {
+    if (ok && staged && sane) {
       if (dst + rec > A.cap) {
         if (lane == 0) atomicOr(A.err, kErrSmall);
       } else {

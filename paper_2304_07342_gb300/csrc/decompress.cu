@@ -17,6 +17,8 @@
 //     positions are resolved by pointer jumping (five shuffle rounds);
 //     older sources are read from a ring of the last >= W+32 decoded
 //     symbols in shared memory (offsets are at most W);
+//   * the record (flags + payload) is first staged into the warp's shared
+//     slice with a TMA bulk copy, so token decoding reads shared memory;
 //   * symbols are stored straight to the output, 32*S contiguous bytes per
 //     warp instruction.
 #include <cuda_runtime.h>
@@ -81,11 +83,46 @@ __device__ __forceinline__ uint64_t record_bytes(const uint8_t *table,
   return warp_sum_u64(part);
 }
 
-__device__ __forceinline__ void decode_chunk(const DecompressArgs &A,
+// Worst-case record of a chunk of k symbols (flags + payload).
+__device__ __forceinline__ uint64_t record_bound(uint64_t k, const Header &h) {
+  const uint64_t extra = (1u + h.offB > h.S * h.m) ? (1u + h.offB - h.S * h.m) : 0u;
+  return (k + 7) / 8 + static_cast<uint64_t>(h.S) * k + extra * (k / h.m);
+}
+
+// Copy record bytes [src, src + n) into the warp's window so that the copy
+// is 16-byte aligned on both sides: head and tail with plain loads, the
+// middle with one TMA bulk copy.  Returns the shared address of byte 0.
+__device__ __forceinline__ const uint8_t *stage_record(const uint8_t *src,
+                                                       uint32_t n, uint8_t *win,
+                                                       uint64_t *bar,
+                                                       uint32_t &phase,
+                                                       uint32_t lane, bool &ok) {
+  const uint32_t mis = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 15u);
+  uint8_t *dst = win + mis;
+  const uint32_t head = min(n, (16u - mis) & 15u);
+  const uint32_t bulk = (n - head) & ~15u;
+  if (bulk && lane == 0) {
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, bulk);
+    bulk_g2s(dst + head, src + head, bulk, bar);
+  }
+  for (uint32_t i = lane; i < head; i += 32) dst[i] = src[i];
+  for (uint32_t i = head + bulk + lane; i < n; i += 32) dst[i] = src[i];
+  ok = true;
+  if (bulk) {
+    ok = mbar_wait_bounded(bar, phase);
+    phase ^= 1u;
+  }
+  __syncwarp();
+  return dst;
+}
+
+__device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
                                              const Header &h, uint32_t c,
                                              uint64_t records_at,
                                              uint32_t *ring, uint32_t rmask,
-                                             uint32_t lane) {
+                                             uint8_t *win, uint64_t *bar,
+                                             uint32_t &phase, uint32_t lane) {
   const uint8_t *in = A.in;
   const uint8_t *table = in + kHeaderBytes;
   const uint8_t *index = table + 8ull * h.nc;
@@ -107,12 +144,22 @@ __device__ __forceinline__ void decode_chunk(const DecompressArgs &A,
   const uint32_t k = static_cast<uint32_t>(
       ((c + 1 < h.nc) ? h.C : h.n - chunk_at) / h.S);
   bad = bad || idxv > A.in_bytes || rec_at + fb + pay > A.in_bytes ||
-        rec_at + fb + pay < rec_at || ntok > k || (ntok == 0 && k > 0);
+        rec_at + fb + pay < rec_at || ntok > k || (ntok == 0 && k > 0) ||
+        fb + pay > record_bound(k, h);
   if (bad) {
     if (lane == 0) atomicOr(A.err, kErrCorrupt);
-    return;
+    return true;
   }
-  const uint8_t *flags = in + rec_at;
+  const uint8_t *flags = in + rec_at;  // read in place when there is no window
+  if (win) {
+    bool staged;
+    flags = stage_record(in + rec_at, static_cast<uint32_t>(fb + pay), win, bar, phase,
+                         lane, staged);
+    if (!staged) {
+      if (lane == 0) atomicOr(A.err, kErrTimeout);
+      return false;
+    }
+  }
   const uint8_t *payload = flags + fb;
   uint8_t *dst = A.out + chunk_at;
   const uint32_t S = h.S, offB = h.offB, tsz = 1 + h.offB;
@@ -157,7 +204,7 @@ __device__ __forceinline__ void decode_chunk(const DecompressArgs &A,
     tbad = tbad || pos + group_len > k;
     if (__any_sync(kFull, tbad)) {
       if (lane == 0) atomicOr(A.err, kErrCorrupt);
-      return;
+      return true;
     }
     const uint32_t end = pos + group_len;
     if (mm == 0) {
@@ -206,16 +253,16 @@ __device__ __forceinline__ void decode_chunk(const DecompressArgs &A,
   if (pos != k || pay_used != pay) {
     if (lane == 0) atomicOr(A.err, kErrCorrupt);
   }
+  return true;
 }
 
 }  // namespace
 
 __global__ void __launch_bounds__(256) decompress_kernel(const DecompressArgs A) {
-  extern __shared__ __align__(16) uint8_t smem[];
+  extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t wpb = blockDim.x >> 5;
-  uint32_t *ring = reinterpret_cast<uint32_t *>(smem + warp * A.per_warp);
 
   Header h;
   const bool ok = read_header(A.in, h);
@@ -234,26 +281,45 @@ __global__ void __launch_bounds__(256) decompress_kernel(const DecompressArgs A)
     if (leader) atomicOr(A.err, kErrCorrupt);
     return;
   }
-  // ring of decoded symbols: a power of two >= W + 32 entries
+  if (leader) *A.out_bytes = h.n;
+  // per-warp slice, decided from the header: mbarrier, a ring of >= W + 32
+  // decoded symbols (offsets are at most W), and a window for one record
   uint32_t ring_n = 64;
   while (ring_n < h.W + 32) ring_n <<= 1;
   const uint32_t rmask = ring_n - 1;
+  const uint64_t kfull = h.C / h.S;
+  uint64_t need = 16 + 4ull * ring_n + ((record_bound(kfull, h) + 32 + 15) & ~15ull);
+  // a record too large for one warp's window is read from global memory
+  const bool windowed = need <= A.smem_bytes;
+  if (!windowed) need = 16 + 4ull * ring_n;
+  const uint64_t fit = A.smem_bytes / need;
+  const uint32_t active = fit < wpb ? static_cast<uint32_t>(fit) : wpb;
+  if (warp >= active) return;
+  uint8_t *ws = smem + warp * need;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(ws);
+  uint32_t *ring = reinterpret_cast<uint32_t *>(ws + 16);
+  uint8_t *win = windowed ? ws + 16 + 4ull * ring_n : nullptr;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  uint32_t phase = 0;
 
-  const uint32_t gw = blockIdx.x * wpb + warp;
-  const uint32_t nwarps = gridDim.x * wpb;
+  const uint32_t gw = blockIdx.x * active + warp;
+  const uint32_t nwarps = gridDim.x * active;
   for (uint32_t c = gw; c < h.nc; c += nwarps)
-    decode_chunk(A, h, c, records_at, ring, rmask, lane);
-  if (leader) *A.out_bytes = h.n;
+    if (!decode_chunk(A, h, c, records_at, ring, rmask, win, bar, phase, lane)) break;
 }
 
-// Shared bytes per warp: a ring of up to 2048 u32 symbols (W <= 1024).
-constexpr uint32_t kDecodeRingBytes = 2048 * 4;
+// Shared memory per block; each warp takes a slice sized from the header.
+constexpr uint32_t kDecodeSmemPerBlock = 72 * 1024;
 
 cudaError_t launch_decompress(DecompressArgs A, int block, cudaStream_t stream) {
   static std::mutex mu;
   static int per_sm = 0, sms = 0, cached_block = -1;
-  A.per_warp = kDecodeRingBytes;
-  const size_t smem = static_cast<size_t>(A.per_warp) * (block / 32);
+  A.smem_bytes = kDecodeSmemPerBlock;
+  const size_t smem = kDecodeSmemPerBlock;
   {
     std::lock_guard<std::mutex> lock(mu);
     if (cached_block != block) {
@@ -273,7 +339,7 @@ cudaError_t launch_decompress(DecompressArgs A, int block, cudaStream_t stream) 
     }
   }
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  // enough warps for the largest stream the input could hold, capped at the
+  // enough blocks for the largest stream the input could hold, capped at the
   // resident limit (the grid cannot depend on the header: it is on the GPU)
   const uint64_t max_chunks = A.in_bytes / kTableEntry + 1;
   const uint64_t warps = block / 32;

@@ -16,6 +16,7 @@ constexpr uint32_t kMaxWindow = 1024;   // symbols
 constexpr uint32_t kErrSmall = 1u << 0;
 constexpr uint32_t kErrCorrupt = 1u << 1;
 constexpr uint32_t kErrTimeout = 1u << 2;
+constexpr uint32_t kErrInternal = 1u << 3;  // a device consistency check failed
 
 // Bounded spins: a device wait that exceeds this many polls gives up and
 // raises kErrTimeout instead of hanging the GPU.
@@ -25,8 +26,10 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 // warp's slice; every region 16-byte aligned).
 struct CompressSmem {
   uint32_t in_off;     // staged chunk, C bytes
+  uint32_t prev_off;   // u16 per position: previous position, same key hash
   uint32_t flags_off;  // flag bits of up to k tokens
   uint32_t pay_off;    // payload staging (worst case); also hash table
+  uint32_t pay_bytes;  // size of the payload staging region
   uint32_t maybe_off;  // one bit per position: a match of >= m may exist
   uint32_t mbar_off;   // mbarrier for the TMA bulk copy
   uint32_t per_warp;   // total bytes per warp
@@ -56,8 +59,8 @@ struct DecompressArgs {
   uint64_t out_cap;
   unsigned long long *out_bytes;
   uint32_t *err;
-  uint32_t per_warp;  // shared bytes per warp (ring of decoded symbols)
-  int out_aligned;    // out is 16-byte aligned
+  uint32_t smem_bytes;  // dynamic shared memory per block
+  int out_aligned;      // out is 16-byte aligned
 };
 
 }  // namespace glz

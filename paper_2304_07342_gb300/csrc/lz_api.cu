@@ -48,6 +48,8 @@ static cudaError_t launch_header(uint8_t *out, uint32_t S, uint32_t offB,
 struct lz_ctx {
   int device = 0;
   int smem_optin = 0;       // max dynamic shared memory per block (bytes)
+  int smem_per_sm = 0;      // shared memory per multiprocessor (bytes)
+  int smem_reserved = 0;    // shared memory the runtime reserves per block
   void *scratch = nullptr;  // [0,16): work counter; [16, ...): status words
   size_t scratch_bytes = 0;
   uint32_t *d_err = nullptr;
@@ -92,10 +94,13 @@ glz::CompressSmem compress_layout(const lz_params *p) {
   uint32_t at = 0;
   sm.in_off = at;
   at += round16(C);
+  sm.prev_off = at;
+  at += round16((p->window > 255 ? 2ull : 1ull) * k);
   sm.flags_off = at;
-  at += round16(div_up(k, 8));
+  at += round16(div_up(k, 32) * 4);
   sm.pay_off = at;
   const uint32_t pay_region = round16(pay_bytes + 16);
+  sm.pay_bytes = pay_region;
   at += pay_region;
   sm.maybe_off = at;
   at += round16(div_up(k, 32) * 4);
@@ -147,6 +152,7 @@ const char *lz_status_string(lz_status s) {
     case LZ_ERR_NOMEM: return "LZ_ERR_NOMEM";
     case LZ_ERR_CUDA: return "LZ_ERR_CUDA";
     case LZ_ERR_TIMEOUT: return "LZ_ERR_TIMEOUT";
+    case LZ_ERR_INTERNAL: return "LZ_ERR_INTERNAL";
   }
   return "LZ_ERR_UNKNOWN";
 }
@@ -180,6 +186,12 @@ lz_status lz_create(lz_ctx **out, int device) {
   ctx->device = device;
   cudaError_t e = cudaDeviceGetAttribute(&ctx->smem_optin,
                                          cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&ctx->smem_per_sm,
+                               cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&ctx->smem_reserved,
+                               cudaDevAttrReservedSharedMemoryPerBlock, device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, 256);
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, 256);
   if (e != cudaSuccess) {
@@ -257,10 +269,21 @@ lz_status lz_compress(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
   A.err = ctx->d_err;
   uint32_t nj = 1;
   while (32 * nj < p->window) nj *= 2;
-  int warps = kCompressWarps;
-  while (warps > 1 && static_cast<int64_t>(A.sm.per_warp) * warps > ctx->smem_optin) --warps;
   if (static_cast<int64_t>(A.sm.per_warp) > ctx->smem_optin) return LZ_ERR_INVALID_ARG;
-  const int block = 32 * warps;
+  // warps per block: the choice that keeps the most warps resident under the
+  // per-SM shared-memory limit (each block also reserves some shared memory)
+  int block = 32, best_warps = 0;
+  for (int wpb = 1; wpb <= kCompressWarps; wpb *= 2) {
+    const int64_t per_block = static_cast<int64_t>(A.sm.per_warp) * wpb + ctx->smem_reserved;
+    if (per_block - ctx->smem_reserved > ctx->smem_optin) break;
+    int64_t blocks = ctx->smem_per_sm / per_block;
+    if (blocks > 32) blocks = 32;
+    const int64_t warps = blocks * wpb;
+    if (warps > best_warps) {
+      best_warps = static_cast<int>(warps);
+      block = 32 * wpb;
+    }
+  }
   switch (S) {
     case 1: e = glz::launch_compress_s1(A, nj, block, st); break;
     case 2: e = glz::launch_compress_s2(A, nj, block, st); break;
@@ -327,6 +350,7 @@ lz_status lz_sync(lz_ctx *ctx, lz_stream_t stream) {
   if (cudaMemsetAsync(ctx->d_err, 0, 4, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return LZ_ERR_CUDA;
+  if (h & glz::kErrInternal) return LZ_ERR_INTERNAL;
   if (h & glz::kErrTimeout) return LZ_ERR_TIMEOUT;
   if (h & glz::kErrCorrupt) return LZ_ERR_CORRUPT;
   return LZ_ERR_BUFFER_TOO_SMALL;

@@ -22,10 +22,11 @@ LZ_ERR_CORRUPT = 3
 LZ_ERR_NOMEM = 4
 LZ_ERR_CUDA = 5
 LZ_ERR_TIMEOUT = 6
+LZ_ERR_INTERNAL = 7
 
 _NAMES = {0: "LZ_OK", 1: "LZ_ERR_INVALID_ARG", 2: "LZ_ERR_BUFFER_TOO_SMALL",
           3: "LZ_ERR_CORRUPT", 4: "LZ_ERR_NOMEM", 5: "LZ_ERR_CUDA",
-          6: "LZ_ERR_TIMEOUT"}
+          6: "LZ_ERR_TIMEOUT", 7: "LZ_ERR_INTERNAL"}
 
 # every symbol include/lz.h declares
 EXPORTS = ("lz_create", "lz_destroy", "lz_status_string", "lz_check_params",

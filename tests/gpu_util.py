@@ -19,7 +19,7 @@ def to_dev(x: np.ndarray, offset: int = 0):
     """Device copy of x's bytes starting `offset` bytes into a fresh buffer
     (offset != 0 gives a misaligned device pointer)."""
     import torch
-    b = np.ascontiguousarray(x).view(np.uint8).reshape(-1)
+    b = np.array(x, copy=True).view(np.uint8).reshape(-1)
     buf = torch.empty(b.size + offset + 16, dtype=torch.uint8, device="cuda")
     view = buf[offset:offset + b.size]
     view.copy_(torch.from_numpy(b))

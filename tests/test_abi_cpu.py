@@ -57,7 +57,7 @@ def test_check_params_matches_oracle(lib):
 def test_status_strings(lib):
     for code, name in [(0, "LZ_OK"), (1, "LZ_ERR_INVALID_ARG"), (2, "LZ_ERR_BUFFER_TOO_SMALL"),
                        (3, "LZ_ERR_CORRUPT"), (4, "LZ_ERR_NOMEM"), (5, "LZ_ERR_CUDA"),
-                       (6, "LZ_ERR_TIMEOUT")]:
+                       (6, "LZ_ERR_TIMEOUT"), (7, "LZ_ERR_INTERNAL")]:
         assert lz.lz_status_string(code) == name
 
 

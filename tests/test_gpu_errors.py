@@ -124,7 +124,7 @@ def test_invalid_arguments(codec):
     x = torch.zeros(64, dtype=torch.uint8, device="cuda")
     out = torch.empty(4096, dtype=torch.uint8, device="cuda")
     ob = torch.zeros(2, dtype=torch.int64, device="cuda")
-    bad_params = [lz.Params(3, 4096, 128, 3), lz.Params(2, 4000, 128, 3),
+    bad_params = [lz.Params(3, 4096, 128, 3), lz.Params(2, 4008, 128, 3), lz.Params(2, 32784, 128, 3),
                   lz.Params(2, 4096, 0, 3), lz.Params(2, 4096, 2000, 3),
                   lz.Params(2, 4096, 128, 0), lz.Params(2, 4096, 128, 9, 8)]
     for P in bad_params:
