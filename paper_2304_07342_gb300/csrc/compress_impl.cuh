@@ -89,34 +89,48 @@ __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
   const uint32_t tshift = 64u - A.sm.hash_log2;
   const uint32_t lt = lanemask_lt(lane);
   const uint32_t nslab = (k + 31) / 32;
-  for (uint32_t s = 0; s < nslab; ++s) {
-    const uint32_t p = s * 32 + lane;
-    const bool ok = p + A.m <= k;  // room for m symbols
-    uint64_t key = 0;
-    if (ok) {
+  constexpr uint32_t kGroup = 4;  // slabs whose hashes are formed together
+  for (uint32_t s0 = 0; s0 < nslab; s0 += kGroup) {
+    // independent part for kGroup slabs: keys, hashes, same-hash lane groups
+    uint32_t hh[kGroup], gg[kGroup];
+    bool okk[kGroup];
 #pragma unroll
-      for (uint32_t i = 0; i < 8u / S; ++i)
-        if (i < g) key |= static_cast<uint64_t>(sym[p + i]) << (8 * S * i);
+    for (uint32_t u = 0; u < kGroup; ++u) {
+      const uint32_t p = (s0 + u) * 32 + lane;
+      const bool ok = s0 + u < nslab && p + A.m <= k;  // room for m symbols
+      uint64_t key = 0;
+      if (ok) {
+#pragma unroll
+        for (uint32_t i = 0; i < 8u / S; ++i)
+          if (i < g) key |= static_cast<uint64_t>(sym[p + i]) << (8 * S * i);
+      }
+      hh[u] = static_cast<uint32_t>((key * 0x9E3779B97F4A7C15ull) >> tshift);
+      okk[u] = ok;
+      gg[u] = (s0 + u < nslab) ? __match_any_sync(kFull, ok ? hh[u] : (0x10000u + lane)) : 0u;
     }
-    const uint32_t h = static_cast<uint32_t>((key * 0x9E3779B97F4A7C15ull) >> tshift);
-    const uint32_t grp = __match_any_sync(kFull, ok ? h : (0x10000u + lane));
-    const uint32_t lower = grp & lt;
-    const uint32_t q = lower ? s * 32 + (31u - __clz(lower)) : table[h];
-    const uint32_t dist = (ok && q != kNoPos && p - q <= A.W) ? p - q : 0u;
-    __syncwarp();
-    if (ok) {
-      links.set(p, dist);
-      if ((grp >> lane) == 1u) table[h] = static_cast<uint16_t>(p);
+    // serial part: the table carries the last position of each hash
+#pragma unroll
+    for (uint32_t u = 0; u < kGroup; ++u) {
+      if (s0 + u >= nslab) break;
+      const uint32_t p = (s0 + u) * 32 + lane;
+      const uint32_t lower = gg[u] & lt;
+      const uint32_t q = lower ? (s0 + u) * 32 + (31u - __clz(lower)) : table[hh[u]];
+      const uint32_t dist = (okk[u] && q != kNoPos && p - q <= A.W) ? p - q : 0u;
+      __syncwarp();
+      if (okk[u]) {
+        links.set(p, dist);
+        if ((gg[u] >> lane) == 1u) table[hh[u]] = static_cast<uint16_t>(p);
+      }
+      const uint32_t bits = __ballot_sync(kFull, dist != 0);
+      if (lane == 0) maybe[s0 + u] = bits;
+      __syncwarp();
     }
-    const uint32_t bits = __ballot_sync(kFull, dist != 0);
-    if (lane == 0) maybe[s] = bits;
-    __syncwarp();
   }
 }
 
 __device__ __forceinline__ void warp_copy_bytes(uint8_t *dst, const uint8_t *src,
                                                 uint32_t nbytes, uint32_t lane) {
-  for (uint32_t i = lane; i < nbytes; i += 32) dst[i] = src[i];
+  warp_copy(dst, src, nbytes, lane);
 }
 
 // Length of the match at p from offset d (d >= 1), at most `cap` symbols.
@@ -359,26 +373,41 @@ __device__ __forceinline__ void greedy_walk(const typename SymType<S>::T *sym,
       o[0] = static_cast<uint8_t>(L);
       o[1] = static_cast<uint8_t>((bd - 1) & 0xFF);
       if (A.offB == 2) o[2] = static_cast<uint8_t>((bd - 1) >> 8);
-    } else if (isv) {
+    }
+    // literal stretches: a visited literal whose previous visited lane is a
+    // pointer (or that is first) starts a run of literal symbols that lasts
+    // until the next visited pointer (or the end of the batch); its bytes
+    // are contiguous in both the chunk and the payload
+    const uint32_t mmask = __ballot_sync(kFull, is_match);
+    const uint32_t before = visited & lanemask_lt(lane);
+    const uint32_t pv = before ? 31u - __clz(before) : lane;
+    const bool starts = isv && !is_match && (before == 0 || ((mmask >> pv) & 1u));
+    const uint32_t later_m = mmask & ~((2u << lane) - 1u);  // pointers after this lane
+    const uint32_t nm = later_m ? __ffs(later_m) - 1 : lane;
+    const uint32_t nm_pos = __shfl_sync(kFull, mypos, nm);
+    const uint32_t s_end = later_m ? nm_pos : after;
+    const uint32_t sb = starts ? (s_end - mypos) * S : 0u;
+    if (starts && sb <= 32) {
       uint8_t *o = pay + pb + b_off;
       const uint8_t *src = in_bytes + mypos * S;
-#pragma unroll
-      for (int i = 0; i < S; ++i) o[i] = src[i];
+      for (uint32_t i = 0; i < sb; ++i) o[i] = src[i];
     }
-    // literal runs: short ones by their lane, long ones by the warp
-    const uint32_t rb = run * S;
-    if (isv && rb > 0 && rb <= 32) {
+    // a pointer's own literal run (when the next visited lane is a pointer
+    // too, or it is the last) is copied by its lane or by the warp
+    const uint32_t rb = is_match ? run * S : 0u;
+    if (rb > 0 && rb <= 32) {
       uint8_t *o = pay + pb + b_off + tsz;
       const uint8_t *src = in_bytes + nxt * S;
       for (uint32_t i = 0; i < rb; ++i) o[i] = src[i];
     }
-    uint32_t longs = __ballot_sync(kFull, isv && rb > 32);
+    uint32_t longs = __ballot_sync(kFull, (starts && sb > 32) || rb > 32);
     while (longs) {
       const uint32_t i = __ffs(longs) - 1;
       longs &= longs - 1;
-      const uint32_t o = __shfl_sync(kFull, pb + b_off + tsz, i);
-      const uint32_t src = __shfl_sync(kFull, nxt * S, i);
-      const uint32_t nb = __shfl_sync(kFull, rb, i);
+      const bool st_i = __shfl_sync(kFull, starts ? 1u : 0u, i) != 0;
+      const uint32_t o = __shfl_sync(kFull, st_i ? pb + b_off : pb + b_off + tsz, i);
+      const uint32_t src = __shfl_sync(kFull, st_i ? mypos * S : nxt * S, i);
+      const uint32_t nb = __shfl_sync(kFull, st_i ? sb : rb, i);
       warp_copy_bytes(pay + o, in_bytes + src, nb, lane);
     }
     __syncwarp();
@@ -392,46 +421,110 @@ __device__ __forceinline__ void greedy_walk(const typename SymType<S>::T *sym,
 
 // Step 4: decoupled look-back (single-pass scan over chunks).  Status word:
 // bit 63 = inclusive prefix, bit 62 = aggregate only, low bits = value;
-// 0 = not published yet.  Returns the exclusive prefix of record bytes.
-__device__ __forceinline__ uint64_t chunk_lookback(unsigned long long *status,
-                                                   uint32_t c, uint64_t agg,
-                                                   uint32_t lane, uint32_t *err,
-                                                   bool &ok) {
-  constexpr unsigned long long kPrefix = 1ull << 63, kAgg = 1ull << 62;
-  constexpr unsigned long long kVal = kAgg - 1;
-  ok = true;
-  if (c == 0) {
-    if (lane == 0) st_relaxed_u64(&status[0], kPrefix | agg);
-    return 0;
-  }
-  if (lane == 0) st_relaxed_u64(&status[c], kAgg | agg);
-  uint64_t excl = 0;
+// 0 = not published yet.
+constexpr unsigned long long kPrefix = 1ull << 63, kAgg = 1ull << 62;
+constexpr unsigned long long kVal = kAgg - 1;
+constexpr uint32_t kLookbackRounds = 8;  // windows of 32 per attempt
+constexpr uint32_t kFreeSlot = 0xFFFFFFFFu;
+
+__device__ __forceinline__ void publish(unsigned long long *status, uint32_t c,
+                                        unsigned long long flag, uint64_t v,
+                                        uint32_t lane) {
+  if (lane == 0) st_relaxed_u64(&status[c], flag | v);
+}
+
+// One non-blocking look-back attempt for chunk c: sum the published
+// aggregates of the chunks before it back to the nearest published
+// inclusive prefix.  False if a chunk it needs has not published yet (or
+// the prefix is more than kLookbackRounds windows back).
+__device__ __forceinline__ bool lookback_try(const unsigned long long *status,
+                                             uint32_t c, uint32_t lane,
+                                             uint64_t &excl,
+                                             uint32_t max_rounds = kLookbackRounds) {
+  excl = 0;
+  if (c == 0) return true;
   int64_t base = static_cast<int64_t>(c) - 1;
-  uint32_t spins = 0, nap = 32;
-  while (true) {
+  for (uint32_t r = 0; r < max_rounds; ++r) {
     const int64_t idx = base - static_cast<int64_t>(lane);
     const unsigned long long v = idx >= 0 ? ld_relaxed_u64(&status[idx]) : kPrefix;
     const uint32_t pref = __ballot_sync(kFull, (v & kPrefix) != 0);
     const uint32_t empty = __ballot_sync(kFull, v == 0);
     const uint32_t limit = pref ? __ffs(pref) - 1 : 31u;
     const uint32_t need = limit == 31 ? kFull : ((2u << limit) - 1u);
-    if (empty & need) {
-      if (++spins > kSpinLimit) {
-        ok = false;
-        if (lane == 0) atomicOr(err, kErrTimeout);
-        break;
-      }
-      __nanosleep(nap);
-      nap = min(nap * 2, 1024u);
-      continue;
-    }
+    if (empty & need) return false;
     excl += warp_sum_u64(lane <= limit ? (v & kVal) : 0ull);
-    if (pref) break;
+    if (pref) return true;
     base -= 32;
   }
-  // a timed-out chunk still publishes so that its successors do not wait
-  if (lane == 0) st_relaxed_u64(&status[c], kPrefix | (excl + agg));
-  return excl;
+  return false;
+}
+
+// Blocking look-back: retry with exponential back-off; after kSpinLimit
+// attempts give up, raise kErrTimeout and return false.  Each attempt scans
+// back as far as needed: every chunk publishes its aggregate as soon as its
+// parse is done, so a full scan only ever waits on chunks still parsing, and
+// chunk 0 always holds a prefix.
+__device__ __forceinline__ bool lookback_wait(const unsigned long long *status,
+                                              uint32_t c, uint32_t lane,
+                                              uint32_t *err, uint64_t &excl) {
+  uint32_t nap = 32;
+  for (uint32_t spins = 0; spins < kSpinLimit; ++spins) {
+    if (lookback_try(status, c, lane, excl, 0xFFFFFFFFu)) return true;
+    __nanosleep(nap);
+    nap = min(nap * 2, 1024u);
+  }
+  if (lane == 0) atomicOr(err, kErrTimeout);
+  return false;
+}
+
+// Step 5 for a chunk whose global offset is known: publish its inclusive
+// prefix, its index entry (every 64th chunk), the stream size (last chunk)
+// and copy its record (from shared staging or a parking slot).
+__device__ __forceinline__ void place_record(const CompressArgs &A, uint32_t c,
+                                             uint64_t excl, uint64_t rec,
+                                             const uint8_t *src1, uint32_t n1,
+                                             const uint8_t *src2, uint32_t n2,
+                                             bool data_ok, uint32_t lane) {
+  publish(A.status, c, kPrefix, excl + rec, lane);
+  if (c % kIndexStride == 0) {
+    uint8_t *idx = A.out + kHeaderBytes + static_cast<uint64_t>(kTableEntry) * A.nc +
+                   8ull * (c / kIndexStride);
+    st_le_bytes(idx, excl, 8, lane);
+  }
+  const uint64_t dst = A.records_at + excl;
+  if (c + 1 == A.nc && lane == 0) *A.out_bytes = dst + rec;
+  if (!data_ok) return;
+  if (dst + rec > A.cap) {
+    if (lane == 0) atomicOr(A.err, kErrSmall);
+    return;
+  }
+  uint8_t *o = A.out + dst;
+  warp_copy(o, src1, n1, lane);
+  if (n2) warp_copy(o + n1, src2, n2, lane);
+}
+
+// Parking slots of this warp whose chunk can now be placed are placed and
+// freed; with `wait`, every occupied slot is placed (blocking).
+__device__ __forceinline__ void drain_parked(const CompressArgs &A, uint8_t *slots,
+                                             uint32_t &slot_c, uint32_t &slot_rec,
+                                             bool wait, uint32_t lane) {
+  for (uint32_t sidx = 0; sidx < A.park_slots; ++sidx) {
+    const uint32_t cs = __shfl_sync(kFull, slot_c, sidx);
+    if (cs == kFreeSlot) continue;
+    const uint32_t rs = __shfl_sync(kFull, slot_rec, sidx);
+    uint64_t excl;
+    bool ok = lookback_try(A.status, cs, lane, excl);
+    bool data_ok = true;
+    if (!ok && wait) {
+      ok = true;
+      data_ok = lookback_wait(A.status, cs, lane, A.err, excl);
+    }
+    if (!ok) continue;
+    const uint8_t *slot = slots + static_cast<uint64_t>(sidx) * A.park_slot_bytes;
+    place_record(A, cs, excl, rs, slot, rs, nullptr, 0, data_ok, lane);
+    if (lane == sidx) slot_c = kFreeSlot;
+    __syncwarp();
+  }
 }
 
 template <int S, int NJ>
@@ -455,6 +548,10 @@ __global__ void __launch_bounds__(256) compress_kernel(const CompressArgs A) {
   }
   __syncwarp();
   uint32_t phase = 0;
+  // this warp's parking slots (lane s < park_slots describes slot s)
+  const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + warp;
+  uint8_t *slots = A.park + gw * A.park_slots * A.park_slot_bytes;
+  uint32_t slot_c = kFreeSlot, slot_rec = 0;
 
   while (true) {
     uint32_t c = 0;
@@ -490,6 +587,11 @@ __global__ void __launch_bounds__(256) compress_kernel(const CompressArgs A) {
     const uint32_t k = bytes / S;
     const uint8_t *src = A.in + chunk_at;
     const uint32_t bulk = A.in_aligned ? (bytes & ~15u) : 0u;
+    if (lane == 0 && A.in_aligned) {
+      // warm L2 for the chunk a wave of warps ahead (whichever warp takes it)
+      const uint64_t ahead = static_cast<uint64_t>(c) + gridDim.x * (blockDim.x >> 5);
+      if (ahead + 1 < A.nc) prefetch_l2(A.in + ahead * A.C, A.C);
+    }
     if (bulk && lane == 0) {
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(bar, bulk);
@@ -518,37 +620,43 @@ __global__ void __launch_bounds__(256) compress_kernel(const CompressArgs A) {
     const uint32_t fb = (ntok + 7) / 8;
     const uint64_t rec = static_cast<uint64_t>(fb) + pb;
 
-    // 4. global offset
-    bool ok;
-    const uint64_t excl = chunk_lookback(A.status, c, rec, lane, A.err, ok);
-
-    // 5. table, index, record
+    // 4. global offset: publish the aggregate at once, so that no other
+    // chunk waits on this warp; place the record now if the offset is
+    // known, else park it and move on (placed after a later chunk)
+    const bool data_ok = staged && sane;
+    if (c != 0) publish(A.status, c, kAgg, rec, lane);
     uint8_t *tab = A.out + kHeaderBytes + static_cast<uint64_t>(kTableEntry) * c;
     if (lane < 4)
       tab[lane] = static_cast<uint8_t>(ntok >> (8 * lane));
     else if (lane < 8)
       tab[lane] = static_cast<uint8_t>(pb >> (8 * (lane - 4)));
-    if (c % kIndexStride == 0) {
-      uint8_t *idx = A.out + kHeaderBytes + static_cast<uint64_t>(kTableEntry) * A.nc +
-                     8ull * (c / kIndexStride);
-      st_le_bytes(idx, excl, 8, lane);
-    }
-    const uint64_t dst = A.records_at + excl;
-    if (ok && staged && sane) {
-      if (dst + rec > A.cap) {
-        if (lane == 0) atomicOr(A.err, kErrSmall);
+    drain_parked(A, slots, slot_c, slot_rec, false, lane);
+    uint64_t excl;
+    if (lookback_try(A.status, c, lane, excl)) {
+      place_record(A, c, excl, rec, flags, fb, pay, pb, data_ok, lane);
+    } else {
+      const uint32_t free_mask =
+          __ballot_sync(kFull, lane < A.park_slots && slot_c == kFreeSlot);
+      if (free_mask && data_ok) {
+        const uint32_t sidx = __ffs(free_mask) - 1;
+        uint8_t *slot = slots + static_cast<uint64_t>(sidx) * A.park_slot_bytes;
+        warp_copy(slot, flags, fb, lane);
+        warp_copy(slot + fb, pay, pb, lane);
+        if (lane == sidx) {
+          slot_c = c;
+          slot_rec = static_cast<uint32_t>(rec);
+        }
       } else {
-        uint8_t *o = A.out + dst;
-        for (uint32_t i = lane; i < fb; i += 32) o[i] = flags[i];
-        for (uint32_t i = lane; i < pb; i += 32) o[fb + i] = pay[i];
+        const bool ok = lookback_wait(A.status, c, lane, A.err, excl);
+        place_record(A, c, excl, rec, flags, fb, pay, pb, data_ok && ok, lane);
       }
     }
-    if (c + 1 == A.nc && lane == 0) *A.out_bytes = dst + rec;
     __syncwarp();
     // a copy that never landed leaves the barrier phase unknown: stop here
     // (the chunk was still published, so no other warp waits on it)
     if (!staged) break;
   }
+  drain_parked(A, slots, slot_c, slot_rec, true, lane);
 }
 
 }  // namespace glz

@@ -5,7 +5,7 @@
 
 namespace glz {
 cudaError_t launch_compress_s1(const CompressArgs &A, uint32_t nj, int block,
-                               cudaStream_t stream) {
-  return launch_compress_t<1>(A, nj, block, stream);
+                               unsigned grid, cudaStream_t stream) {
+  return launch_compress_t<1>(A, nj, block, grid, stream);
 }
 }  // namespace glz

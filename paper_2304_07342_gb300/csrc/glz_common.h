@@ -50,6 +50,9 @@ struct CompressArgs {
   unsigned long long *status;  // nc look-back words (cleared per call)
   uint32_t *ticket;            // work counter (cleared per call)
   uint32_t *err;               // sticky error bits
+  uint8_t *park;               // parking slots: grid warps x park_slots
+  uint32_t park_slots;         // slots per warp (<= 32)
+  uint32_t park_slot_bytes;    // one worst-case record, 16-byte multiple
 };
 
 struct DecompressArgs {

@@ -73,6 +73,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar,
   return false;
 }
 
+// L2 prefetch of a global range (address and size multiples of 16).
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes)
+               : "memory");
+}
+
 // ---- relaxed device-scope status words -----------------------------------------
 
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p,
@@ -102,6 +108,34 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
+}
+
+// Warp copy of n bytes between any two addresses (shared or global): the
+// destination is written in aligned 32-bit words, each assembled from two
+// aligned source words with a funnel shift; unaligned head and tail bytes
+// are copied singly.  May read up to 3 bytes past the source range (the
+// callers' source regions have that slack).
+__device__ __forceinline__ void warp_copy(uint8_t *dst, const uint8_t *src,
+                                          uint32_t n, uint32_t lane) {
+  const uint32_t head =
+      min(n, (4u - static_cast<uint32_t>(reinterpret_cast<uintptr_t>(dst) & 3u)) & 3u);
+  if (lane < head) dst[lane] = src[lane];
+  const uint32_t words = (n - head) >> 2;
+  if (words) {
+    const uint8_t *sb = src + head;
+    const uint32_t sm = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(sb) & 3u);
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(sb - sm);
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst + head);
+    if (sm == 0) {
+      for (uint32_t j = lane; j < words; j += 32) d32[j] = s32[j];
+    } else {
+      const uint32_t sh = 8u * sm;
+      for (uint32_t j = lane; j < words; j += 32)
+        d32[j] = __funnelshift_r(s32[j], s32[j + 1], sh);
+    }
+  }
+  const uint32_t done = head + 4u * words;
+  if (lane < n - done) dst[done + lane] = src[done + lane];
 }
 
 // Little-endian byte stores/loads usable at any alignment.

@@ -12,11 +12,11 @@
 
 namespace glz {
 cudaError_t launch_compress_s1(const CompressArgs &A, uint32_t nj, int block,
-                               cudaStream_t stream);
+                               unsigned grid, cudaStream_t stream);
 cudaError_t launch_compress_s2(const CompressArgs &A, uint32_t nj, int block,
-                               cudaStream_t stream);
+                               unsigned grid, cudaStream_t stream);
 cudaError_t launch_compress_s4(const CompressArgs &A, uint32_t nj, int block,
-                               cudaStream_t stream);
+                               unsigned grid, cudaStream_t stream);
 cudaError_t launch_decompress(DecompressArgs A, int block, cudaStream_t stream);
 
 // Empty input: the stream is the header alone (n_chunks = 0, n_bytes = 0).
@@ -50,6 +50,7 @@ struct lz_ctx {
   int smem_optin = 0;       // max dynamic shared memory per block (bytes)
   int smem_per_sm = 0;      // shared memory per multiprocessor (bytes)
   int smem_reserved = 0;    // shared memory the runtime reserves per block
+  int sms = 0;              // multiprocessors
   void *scratch = nullptr;  // [0,16): work counter; [16, ...): status words
   size_t scratch_bytes = 0;
   uint32_t *d_err = nullptr;
@@ -59,6 +60,7 @@ struct lz_ctx {
 namespace {
 
 constexpr int kCompressWarps = 4;      // warps per block (fewer if smem-bound)
+constexpr uint32_t kParkSlots = 3;     // parked records per compressing warp
 constexpr int kDecompressBlock = 256;  // 8 warps, one chunk per warp
 constexpr size_t kScratchHead = 16;
 
@@ -192,6 +194,8 @@ lz_status lz_create(lz_ctx **out, int device) {
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&ctx->smem_reserved,
                                cudaDevAttrReservedSharedMemoryPerBlock, device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, 256);
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, 256);
   if (e != cudaSuccess) {
@@ -241,10 +245,34 @@ lz_status lz_compress(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
                                           p->min_match, p->max_match, C,
                                           p->window, out_bytes, st));
 
-  const size_t need = kScratchHead + 8ull * nc;
+  glz::CompressSmem sm = compress_layout(p);
+  if (static_cast<int64_t>(sm.per_warp) > ctx->smem_optin) return LZ_ERR_INVALID_ARG;
+  // warps per block: the choice that keeps the most warps resident under the
+  // per-SM shared-memory limit (each block also reserves some shared memory)
+  int block = 32;
+  int64_t best_warps = 0, best_blocks = 1;
+  for (int wpb = 1; wpb <= kCompressWarps; wpb *= 2) {
+    const int64_t per_block = static_cast<int64_t>(sm.per_warp) * wpb + ctx->smem_reserved;
+    if (per_block - ctx->smem_reserved > ctx->smem_optin) break;
+    int64_t blocks = ctx->smem_per_sm / per_block;
+    if (blocks > 32) blocks = 32;
+    if (blocks * wpb > best_warps) {
+      best_warps = blocks * wpb;
+      best_blocks = blocks;
+      block = 32 * wpb;
+    }
+  }
+  const uint64_t wpb = block / 32;
+  uint64_t grid = div_up(nc, wpb);
+  if (grid > static_cast<uint64_t>(best_blocks) * ctx->sms) grid = best_blocks * ctx->sms;
+  // scratch: work counter, nc status words, parking slots of every warp
+  const uint32_t slot_bytes = round16(div_up(C / S, 8) + sm.pay_bytes + 16);
+  const size_t status_end = kScratchHead + 8ull * nc;
+  const size_t park_at = (status_end + 255) & ~static_cast<size_t>(255);
+  const size_t need = park_at + static_cast<size_t>(slot_bytes) * kParkSlots * wpb * grid;
   lz_status s = reserve_scratch(ctx, need);
   if (s != LZ_OK) return s;
-  cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, need, st);
+  cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, status_end, st);
   if (e != cudaSuccess) return LZ_ERR_CUDA;
 
   glz::CompressArgs A{};
@@ -262,32 +290,21 @@ lz_status lz_compress(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
   A.nc = static_cast<uint32_t>(nc);
   A.records_at = records_at;
   A.in_aligned = (reinterpret_cast<uintptr_t>(d_in) % 16) == 0;
-  A.sm = compress_layout(p);
+  A.sm = sm;
+  A.park = static_cast<uint8_t *>(ctx->scratch) + park_at;
+  A.park_slots = kParkSlots;
+  A.park_slot_bytes = slot_bytes;
   A.ticket = static_cast<uint32_t *>(ctx->scratch);
   A.status = reinterpret_cast<unsigned long long *>(
       static_cast<uint8_t *>(ctx->scratch) + kScratchHead);
   A.err = ctx->d_err;
   uint32_t nj = 1;
   while (32 * nj < p->window) nj *= 2;
-  if (static_cast<int64_t>(A.sm.per_warp) > ctx->smem_optin) return LZ_ERR_INVALID_ARG;
-  // warps per block: the choice that keeps the most warps resident under the
-  // per-SM shared-memory limit (each block also reserves some shared memory)
-  int block = 32, best_warps = 0;
-  for (int wpb = 1; wpb <= kCompressWarps; wpb *= 2) {
-    const int64_t per_block = static_cast<int64_t>(A.sm.per_warp) * wpb + ctx->smem_reserved;
-    if (per_block - ctx->smem_reserved > ctx->smem_optin) break;
-    int64_t blocks = ctx->smem_per_sm / per_block;
-    if (blocks > 32) blocks = 32;
-    const int64_t warps = blocks * wpb;
-    if (warps > best_warps) {
-      best_warps = static_cast<int>(warps);
-      block = 32 * wpb;
-    }
-  }
+  const unsigned g = static_cast<unsigned>(grid);
   switch (S) {
-    case 1: e = glz::launch_compress_s1(A, nj, block, st); break;
-    case 2: e = glz::launch_compress_s2(A, nj, block, st); break;
-    default: e = glz::launch_compress_s4(A, nj, block, st); break;
+    case 1: e = glz::launch_compress_s1(A, nj, block, g, st); break;
+    case 2: e = glz::launch_compress_s2(A, nj, block, g, st); break;
+    default: e = glz::launch_compress_s4(A, nj, block, g, st); break;
   }
   return cuda_status(e);
 }
