@@ -50,18 +50,22 @@ constexpr uint16_t kNoPos = 0xFFFF;  // chunk positions are < 32768
 
 // Chain links: distance from a position to the previous one with the same
 // key hash, 0 if there is none within the window.  One byte per position
-// while W <= 255, two bytes beyond.
+// while W <= 256, two bytes beyond.
+// The stored value is distance - 1; whether a position has a link at all
+// is its bit in the `maybe` mask, so one byte covers windows up to 256.
 struct Links {
   uint8_t *base;
+  const uint32_t *has;  // the `maybe` mask
   bool wide;
   __device__ __forceinline__ uint32_t get(uint32_t p) const {
-    return wide ? reinterpret_cast<const uint16_t *>(base)[p] : base[p];
+    if (!((has[p >> 5] >> (p & 31)) & 1u)) return 0;
+    return 1u + (wide ? reinterpret_cast<const uint16_t *>(base)[p] : base[p]);
   }
-  __device__ __forceinline__ void set(uint32_t p, uint32_t d) const {
+  __device__ __forceinline__ void set(uint32_t p, uint32_t d) const {  // d >= 1
     if (wide)
-      reinterpret_cast<uint16_t *>(base)[p] = static_cast<uint16_t>(d);
+      reinterpret_cast<uint16_t *>(base)[p] = static_cast<uint16_t>(d - 1);
     else
-      base[p] = static_cast<uint8_t>(d);
+      base[p] = static_cast<uint8_t>(d - 1);
   }
 };
 
@@ -72,9 +76,9 @@ struct Links {
 // match of >= m symbols at p from offset d needs p - d to carry the same
 // key, so every such offset is on p's chain, and an unmarked p has none:
 // skipping unmarked positions as literals leaves the greedy parse
-// unchanged.  The table holds the last position per hash;
-// __match_any_sync links the positions of one 32-position slab that share a
-// hash.
+// unchanged.  The table holds the last position per hash; positions of one
+// 32-position slab that share a hash are linked through __match_any_sync
+// lane groups (only in slabs where such a collision occurs).
 template <int S>
 __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
                                              uint32_t k, const CompressArgs &A,
@@ -91,8 +95,8 @@ __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
   const uint32_t nslab = (k + 31) / 32;
   constexpr uint32_t kGroup = 4;  // slabs whose hashes are formed together
   for (uint32_t s0 = 0; s0 < nslab; s0 += kGroup) {
-    // independent part for kGroup slabs: keys, hashes, same-hash lane groups
-    uint32_t hh[kGroup], gg[kGroup];
+    // independent part for kGroup slabs: keys and hashes
+    uint32_t hh[kGroup];
     bool okk[kGroup];
 #pragma unroll
     for (uint32_t u = 0; u < kGroup; ++u) {
@@ -106,21 +110,33 @@ __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
       }
       hh[u] = static_cast<uint32_t>((key * 0x9E3779B97F4A7C15ull) >> tshift);
       okk[u] = ok;
-      gg[u] = (s0 + u < nslab) ? __match_any_sync(kFull, ok ? hh[u] : (0x10000u + lane)) : 0u;
     }
-    // serial part: the table carries the last position of each hash
+    // serial part: the table carries the last position of each hash.  Each
+    // lane reads its bucket, then all lanes write their position and read
+    // it back: a lane that finds another position lost a collision, so its
+    // slab holds two positions with one hash.  Only such slabs need the
+    // lane groups of __match_any_sync (a shared unit with low throughput).
 #pragma unroll
     for (uint32_t u = 0; u < kGroup; ++u) {
       if (s0 + u >= nslab) break;
       const uint32_t p = (s0 + u) * 32 + lane;
-      const uint32_t lower = gg[u] & lt;
-      const uint32_t q = lower ? (s0 + u) * 32 + (31u - __clz(lower)) : table[hh[u]];
-      const uint32_t dist = (okk[u] && q != kNoPos && p - q <= A.W) ? p - q : 0u;
+      const bool ok = okk[u];
+      const uint32_t h = hh[u];
+      const uint32_t old = ok ? table[h] : kNoPos;
       __syncwarp();
-      if (okk[u]) {
-        links.set(p, dist);
-        if ((gg[u] >> lane) == 1u) table[hh[u]] = static_cast<uint16_t>(p);
+      if (ok) table[h] = static_cast<uint16_t>(p);
+      __syncwarp();
+      const bool lost = ok && table[h] != p;
+      uint32_t q = old;
+      if (__any_sync(kFull, lost)) {
+        const uint32_t grp = __match_any_sync(kFull, ok ? h : (0x10000u + lane));
+        const uint32_t lower = grp & lt;
+        if (lower) q = (s0 + u) * 32 + (31u - __clz(lower));
+        __syncwarp();
+        if (ok && (grp >> lane) == 1u) table[h] = static_cast<uint16_t>(p);  // last wins
       }
+      const uint32_t dist = (ok && q != kNoPos && p - q <= A.W) ? p - q : 0u;
+      if (dist) links.set(p, dist);
       const uint32_t bits = __ballot_sync(kFull, dist != 0);
       if (lane == 0) maybe[s0 + u] = bits;
       __syncwarp();
@@ -140,6 +156,31 @@ __device__ __forceinline__ uint32_t extend(const typename SymType<S>::T *sym,
   uint32_t l = 0;
   while (l < cap && sym[p + l] == sym[p - d + l]) ++l;
   return l;
+}
+
+// Little-endian 32-bit word of the chunk starting at byte b (any alignment;
+// reads the aligned words around it).
+__device__ __forceinline__ uint32_t bytes_at(const uint8_t *base, uint32_t b) {
+  const uint32_t *w = reinterpret_cast<const uint32_t *>(base + (b & ~3u));
+  const uint32_t sh = 8u * (b & 3u);
+  return sh ? __funnelshift_r(w[0], w[1], sh) : w[0];
+}
+
+// extend() four bytes at a time: compare 32-bit words of the look-ahead and
+// of the source, and locate the first differing symbol with a bit scan.
+// Reads up to 3 bytes beyond the compared symbols (within the staged chunk
+// region and its slack).
+template <int S>
+__device__ __forceinline__ uint32_t extend_words(const uint8_t *in, uint32_t p,
+                                                 uint32_t d, uint32_t cap) {
+  constexpr uint32_t per = 4 / S;  // symbols per word
+  uint32_t l = 0;
+  while (l < cap) {
+    const uint32_t x = bytes_at(in, (p + l) * S) ^ bytes_at(in, (p - d + l) * S);
+    if (x) return min(cap, l + static_cast<uint32_t>(__ffs(x) - 1) / (8 * S));
+    l += per;
+  }
+  return cap;
 }
 
 // Per-lane work caps of the chain evaluation; a position that needs more
@@ -165,9 +206,10 @@ __device__ __forceinline__ bool chain_match(const typename SymType<S>::T *sym,
     if (hops >= kChainHops || work >= kChainWork) return false;
     if (d >= A.m) {
       const uint32_t cap = min(lim, d);
-      if (cap > best) {
-        const uint32_t l = extend<S>(sym, q, d, cap);
-        work += l + 1;
+      // only a candidate that agrees at index `best` can be longer
+      if (cap > best && sym[q + best] == sym[q - d + best]) {
+        const uint32_t l = extend_words<S>(reinterpret_cast<const uint8_t *>(sym), q, d, cap);
+        work += l / (4 / S) + 1;
         if (l > best) {
           best = l;
           bd = d;
@@ -310,15 +352,22 @@ __device__ __forceinline__ void greedy_walk(const typename SymType<S>::T *sym,
       __syncwarp();
       if (p >= k) break;
     }
-    // batch: lane i <- i-th marked position >= p
-    uint32_t mypos = k, seen = 0, w = p >> 5;
-    uint32_t bits = maybe[w] & (kFull << (p & 31));
-    while (true) {
+    // batch: lane i <- i-th marked position >= p (32 mark words at a time,
+    // a warp scan of their popcounts locates each lane's target)
+    uint32_t mypos = k, seen = 0;
+    for (uint32_t w0 = p >> 5; w0 < nw && seen < 32; w0 += 32) {
+      const uint32_t w = w0 + lane;
+      uint32_t bits = w < nw ? maybe[w] : 0u;
+      if (w == (p >> 5)) bits &= kFull << (p & 31);
       const uint32_t cnt = __popc(bits);
-      if (lane >= seen && lane < seen + cnt) mypos = (w << 5) + nth_set_bit(bits, lane - seen);
-      seen += cnt;
-      if (seen >= 32 || ++w >= nw) break;
-      bits = maybe[w];
+      uint32_t tot;
+      const uint32_t excl = warp_excl_scan(cnt, lane, tot);
+      const uint32_t want = lane - seen;  // this lane's target among these words
+      const uint32_t j = count_below(excl + cnt, want + 1);  // word holding it
+      const uint32_t jb = __shfl_sync(kFull, bits, j < 32 ? j : 0);
+      const uint32_t je = __shfl_sync(kFull, excl, j < 32 ? j : 0);
+      if (lane >= seen && want < tot) mypos = ((w0 + j) << 5) + nth_set_bit(jb, want - je);
+      seen += tot;
     }
     const uint32_t nvalid = min(seen, 32u);
     const bool valid = lane < nvalid;
@@ -329,8 +378,21 @@ __device__ __forceinline__ void greedy_walk(const typename SymType<S>::T *sym,
     uint32_t nxt = valid ? mypos + (L >= A.m ? L : 1u) : k;
     uint32_t succ = count_below(mypos, nxt);
     if (!valid) succ = 32;
-    // serial chase over the visited lanes (exact fallback where needed)
-    uint32_t visited = 0, v = 0;
+    // visited lanes: the chain lane 0, succ(0), succ(succ(0)), ... found by
+    // pointer doubling (lane t computes the t-th element)
+    uint32_t jr = succ;  // succ^(2^r) of this lane, 32 = past the batch
+    uint32_t x = 0;      // for lane t: succ^(t's low bits so far)(0)
+#pragma unroll
+    for (uint32_t r = 0; r < 5; ++r) {
+      const uint32_t xr = __shfl_sync(kFull, jr, x < 32 ? x : 0);
+      if ((lane >> r) & 1u) x = x < 32 ? xr : 32;
+      const uint32_t nj = __shfl_sync(kFull, jr, jr < 32 ? jr : 0);
+      jr = jr < 32 ? nj : 32;
+    }
+    uint32_t visited = __reduce_or_sync(kFull, x < nvalid ? (1u << x) : 0u);
+    // serial chase, only when a visited lane still needs the exact fallback
+    uint32_t v = (visited & unres) ? 0 : nvalid;
+    if (v == 0) visited = 0;
     while (v < nvalid) {
       visited |= 1u << v;
       if ((unres >> v) & 1u) {
@@ -538,7 +600,7 @@ __global__ void __launch_bounds__(256) compress_kernel(const CompressArgs A) {
   uint8_t *flags = ws + A.sm.flags_off;
   uint8_t *pay = ws + A.sm.pay_off;
   uint32_t *maybe = reinterpret_cast<uint32_t *>(ws + A.sm.maybe_off);
-  const Links links{ws + A.sm.prev_off, A.W > 255};
+  const Links links{ws + A.sm.prev_off, maybe, A.W > 256};
   uint64_t *bar = reinterpret_cast<uint64_t *>(ws + A.sm.mbar_off);
   const Sym *sym = reinterpret_cast<const Sym *>(inb);
 

@@ -117,6 +117,38 @@ __device__ __forceinline__ const uint8_t *stage_record(const uint8_t *src,
   return dst;
 }
 
+// 16 bytes of (a, b) starting at byte r (r uniform over the warp).
+__device__ __forceinline__ uint4 bytes16(const uint4 &a, const uint4 &b, uint32_t r) {
+  const uint32_t s = 8u * (r & 3u);
+  uint32_t w0, w1, w2, w3, w4;
+  switch (r >> 2) {
+    case 0: w0 = a.x; w1 = a.y; w2 = a.z; w3 = a.w; w4 = b.x; break;
+    case 1: w0 = a.y; w1 = a.z; w2 = a.w; w3 = b.x; w4 = b.y; break;
+    case 2: w0 = a.z; w1 = a.w; w2 = b.x; w3 = b.y; w4 = b.z; break;
+    default: w0 = a.w; w1 = b.x; w2 = b.y; w3 = b.z; w4 = b.w; break;
+  }
+  if (s == 0) return make_uint4(w0, w1, w2, w3);
+  return make_uint4(__funnelshift_r(w0, w1, s), __funnelshift_r(w1, w2, s),
+                    __funnelshift_r(w2, w3, s), __funnelshift_r(w3, w4, s));
+}
+
+// Warp copy of n bytes from shared src (any alignment, 16 bytes of slack
+// readable past the end) to global dst, 16-byte stores where dst allows.
+__device__ __forceinline__ void copy_s2g(uint8_t *dst, const uint8_t *src,
+                                         uint32_t n, uint32_t lane) {
+  const uint32_t head = min(
+      n, (16u - static_cast<uint32_t>(reinterpret_cast<uintptr_t>(dst) & 15u)) & 15u);
+  if (lane < head) dst[lane] = src[lane];
+  const uint32_t body = (n - head) >> 4;
+  const uint8_t *sb = src + head;
+  const uint32_t r = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(sb) & 15u);
+  const uint4 *s16 = reinterpret_cast<const uint4 *>(sb - r);
+  uint4 *d16 = reinterpret_cast<uint4 *>(dst + head);
+  for (uint32_t j = lane; j < body; j += 32) d16[j] = bytes16(s16[j], s16[j + 1], r);
+  const uint32_t done = head + 16u * body;
+  for (uint32_t i = done + lane; i < n; i += 32) dst[i] = src[i];
+}
+
 __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
                                              const Header &h, uint32_t c,
                                              uint64_t records_at,
@@ -163,6 +195,19 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
   const uint8_t *payload = flags + fb;
   uint8_t *dst = A.out + chunk_at;
   const uint32_t S = h.S, offB = h.offB, tsz = 1 + h.offB;
+  if (win) {
+    // a chunk without pointers is its payload: copy it straight out
+    uint32_t any = 0;
+    for (uint32_t i = lane; i < fb; i += 32) any |= flags[i];
+    if (!__any_sync(kFull, any != 0)) {
+      if (ntok != k || static_cast<uint64_t>(pay) != static_cast<uint64_t>(k) * S) {
+        if (lane == 0) atomicOr(A.err, kErrCorrupt);
+        return true;
+      }
+      copy_s2g(dst, flags + fb, pay, lane);
+      return true;
+    }
+  }
   const bool aligned = A.out_aligned != 0;
   const uint32_t lt = lanemask_lt(lane);
 

@@ -97,7 +97,7 @@ glz::CompressSmem compress_layout(const lz_params *p) {
   sm.in_off = at;
   at += round16(C);
   sm.prev_off = at;
-  at += round16((p->window > 255 ? 2ull : 1ull) * k);
+  at += round16((p->window > 256 ? 2ull : 1ull) * k);
   sm.flags_off = at;
   at += round16(div_up(k, 32) * 4);
   sm.pay_off = at;
