@@ -128,6 +128,26 @@ lz_status lz_decompress(lz_ctx *ctx, const void *d_in, uint64_t in_bytes,
                         void *d_out, uint64_t out_cap, uint64_t *d_out_bytes,
                         lz_stream_t stream);
 
+/* Compression for callers that cannot allocate device memory (no paper
+ * counterpart; an addition of this library).  Same stream as lz_compress,
+ * on the current device, with no context: the scratch is a fixed device
+ * array inside the library (512 KiB + 16 B, held by every GPU that loads
+ * the library until the process exits), so the call allocates nothing and
+ * n_bytes may span at most 65536 chunks (LZ_ERR_INVALID_ARG beyond that).
+ * The caller passes inputs and outputs as for lz_compress.  Device-side
+ * outcomes are reported through *d_out_bytes: a value <= out_cap is the
+ * stream size (success); a value > out_cap is the size that was needed
+ * (output too small, stream incomplete); 0 means a device-side check failed.
+ * Every call shares the fixed array, so calls whose work overlaps on the GPU
+ * (other streams, other threads) race and must not be issued; calls ordered
+ * on one stream are fine.  The first call on a device looks up the array's
+ * device address (and launch limits); make that first call before any
+ * stream capture.  Slower than lz_compress on inputs with uneven chunks: a
+ * chunk whose offset is not yet known waits instead of moving on. */
+lz_status lz_compress_noalloc(const void *d_in, uint64_t n_bytes, const lz_params *p,
+                              void *d_out, uint64_t out_cap, uint64_t *d_out_bytes,
+                              lz_stream_t stream);
+
 /* Synchronise `stream`, then return and clear the context's sticky device
  * error (LZ_OK if none).  When several errors occurred the most severe is
  * returned: INTERNAL, TIMEOUT, CORRUPT, then BUFFER_TOO_SMALL. */

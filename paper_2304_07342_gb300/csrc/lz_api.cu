@@ -374,3 +374,153 @@ lz_status lz_sync(lz_ctx *ctx, lz_stream_t stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Compression that allocates nothing.
+//
+// Some callers cannot allocate device memory at the point where they need to
+// compress: code running inside a custom allocator or an out-of-memory
+// handler, a pre-sized real-time pipeline that forbids allocation after
+// start-up, or a plug-in whose host only lends it buffers.  For them,
+// lz_compress_noalloc takes its scratch (work counter, error word and one
+// look-back status word per chunk) from the fixed device array below, which
+// every GPU that loads this library holds until the process exits.  It runs
+// the regular compression kernel with no parking slots, so a chunk whose
+// offset is not known yet waits for its predecessors instead of moving on.
+
+namespace {
+
+constexpr uint32_t kNoAllocMaxChunks = 65536;  // chunks per call, at most
+constexpr size_t kNoAllocHead = 16;            // [0,4) counter, [4,8) error word
+constexpr size_t kNoAllocBytes = kNoAllocHead + 8ull * kNoAllocMaxChunks;  // 512 KiB + 16
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// If the call's kernel raised an error other than "output too small" (whose
+// needed size is already in *out_bytes), report it as a stream size of 0;
+// clear the word for the next call.
+__global__ void noalloc_report(uint32_t *err, unsigned long long *out_bytes) {
+  if (threadIdx.x == 0 && *err != 0) {
+    if (*err & ~glz::kErrSmall) *out_bytes = 0;
+    *err = 0;
+  }
+}
+
+struct NoAllocDevice {
+  bool ready = false;
+  unsigned char *scratch = nullptr;  // device address of g_noalloc_scratch
+  int smem_optin = 0, smem_per_sm = 0, smem_reserved = 0, sms = 0;
+};
+
+// Per-device set-up, done once with that device current: the device address
+// of the static scratch array (the host-side symbol is only a stand-in) and
+// the launch limits.
+lz_status noalloc_device(int dev, NoAllocDevice **out) {
+  static std::mutex mu;
+  static NoAllocDevice devs[64];
+  if (dev < 0 || dev >= 64) return LZ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(mu);
+  NoAllocDevice &d = devs[dev];
+  if (!d.ready) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
+      return LZ_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&d.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                               dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&d.smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return LZ_ERR_CUDA;
+    d.scratch = static_cast<unsigned char *>(ptr);
+    d.ready = true;
+  }
+  *out = &d;
+  return LZ_OK;
+}
+
+}  // namespace
+
+extern "C" lz_status lz_compress_noalloc(const void *d_in, uint64_t n_bytes,
+                                         const lz_params *p, void *d_out, uint64_t out_cap,
+                                         uint64_t *d_out_bytes, lz_stream_t stream) {
+  if (!params_ok(p) || !d_out || !d_out_bytes) return LZ_ERR_INVALID_ARG;
+  if (n_bytes > 0 && !d_in) return LZ_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(d_out_bytes) % 8 != 0) return LZ_ERR_INVALID_ARG;
+  const uint32_t S = p->symbol_bytes, C = p->chunk_bytes;
+  if (n_bytes % S != 0) return LZ_ERR_INVALID_ARG;
+  const uint64_t nc = div_up(n_bytes, C);
+  if (nc > kNoAllocMaxChunks) return LZ_ERR_INVALID_ARG;  // beyond the fixed scratch
+  const uint64_t records_at = glz::kHeaderBytes + glz::kTableEntry * nc +
+                              8ull * div_up(nc, glz::kIndexStride);
+  if (out_cap < records_at) return LZ_ERR_BUFFER_TOO_SMALL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LZ_ERR_CUDA;
+  NoAllocDevice *nd = nullptr;
+  lz_status s = noalloc_device(dev, &nd);
+  if (s != LZ_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const uint32_t offB = off_bytes(p->window);
+  auto *out_bytes = reinterpret_cast<unsigned long long *>(d_out_bytes);
+  if (nc == 0)
+    return cuda_status(glz::launch_header(static_cast<uint8_t *>(d_out), S, offB,
+                                          p->min_match, p->max_match, C, p->window,
+                                          out_bytes, st));
+  const glz::CompressSmem sm = compress_layout(p);
+  if (static_cast<int64_t>(sm.per_warp) > nd->smem_optin) return LZ_ERR_INVALID_ARG;
+  int block = 32;
+  int64_t best_warps = 0, best_blocks = 1;
+  for (int wpb = 1; wpb <= kCompressWarps; wpb *= 2) {
+    const int64_t per_block = static_cast<int64_t>(sm.per_warp) * wpb + nd->smem_reserved;
+    if (per_block - nd->smem_reserved > nd->smem_optin) break;
+    int64_t blocks = nd->smem_per_sm / per_block;
+    if (blocks > 32) blocks = 32;
+    if (blocks * wpb > best_warps) {
+      best_warps = blocks * wpb;
+      best_blocks = blocks;
+      block = 32 * wpb;
+    }
+  }
+  uint64_t grid = div_up(nc, block / 32);
+  if (grid > static_cast<uint64_t>(best_blocks) * nd->sms) grid = best_blocks * nd->sms;
+  // the counter and the status words must start at zero; the error word is
+  // cleared by the previous call's report (and starts at zero)
+  if (cudaMemsetAsync(nd->scratch + kNoAllocHead, 0, 8ull * nc, st) != cudaSuccess ||
+      cudaMemsetAsync(nd->scratch, 0, 4, st) != cudaSuccess)
+    return LZ_ERR_CUDA;
+  glz::CompressArgs A{};
+  A.in = static_cast<const uint8_t *>(d_in);
+  A.n = n_bytes;
+  A.out = static_cast<uint8_t *>(d_out);
+  A.cap = out_cap;
+  A.out_bytes = out_bytes;
+  A.S = S;
+  A.C = C;
+  A.W = p->window;
+  A.m = p->min_match;
+  A.M = p->max_match;
+  A.offB = offB;
+  A.nc = static_cast<uint32_t>(nc);
+  A.records_at = records_at;
+  A.in_aligned = (reinterpret_cast<uintptr_t>(d_in) % 16) == 0;
+  A.sm = sm;
+  A.park = nullptr;  // no parking slots: blocking look-back
+  A.park_slots = 0;
+  A.park_slot_bytes = 0;
+  A.ticket = reinterpret_cast<uint32_t *>(nd->scratch);
+  A.err = reinterpret_cast<uint32_t *>(nd->scratch + 4);
+  A.status = reinterpret_cast<unsigned long long *>(nd->scratch + kNoAllocHead);
+  uint32_t nj = 1;
+  while (32 * nj < p->window) nj *= 2;
+  cudaError_t e;
+  const unsigned g = static_cast<unsigned>(grid);
+  switch (S) {
+    case 1: e = glz::launch_compress_s1(A, nj, block, g, st); break;
+    case 2: e = glz::launch_compress_s2(A, nj, block, g, st); break;
+    default: e = glz::launch_compress_s4(A, nj, block, g, st); break;
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  noalloc_report<<<1, 32, 0, st>>>(A.err, out_bytes);
+  return cuda_status(cudaGetLastError());
+}

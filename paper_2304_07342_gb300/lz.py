@@ -31,7 +31,7 @@ _NAMES = {0: "LZ_OK", 1: "LZ_ERR_INVALID_ARG", 2: "LZ_ERR_BUFFER_TOO_SMALL",
 # every symbol include/lz.h declares
 EXPORTS = ("lz_create", "lz_destroy", "lz_status_string", "lz_check_params",
            "lz_compressed_bound", "lz_compress", "lz_decompressed_size",
-           "lz_decompress", "lz_sync")
+           "lz_decompress", "lz_sync", "lz_compress_noalloc")
 
 
 class LzError(RuntimeError):
@@ -91,6 +91,8 @@ def load(path: str = LIB_PATH):
     lib.lz_decompress.restype = i32
     lib.lz_sync.argtypes = [vp, vp]
     lib.lz_sync.restype = i32
+    lib.lz_compress_noalloc.argtypes = [vp, u64, pp, vp, u64, vp, vp]
+    lib.lz_compress_noalloc.restype = i32
     _lib = lib
     return lib
 
@@ -141,6 +143,14 @@ def lz_decompress(ctx: int, d_in: int, in_bytes: int, d_out: int, out_cap: int,
                   d_out_bytes: int, stream: int = 0) -> None:
     _check(load().lz_decompress(ctx, d_in, in_bytes, d_out, out_cap,
                                 d_out_bytes, stream), "lz_decompress")
+
+
+def lz_compress_noalloc(d_in: int, n_bytes: int, p: Params, d_out: int, out_cap: int,
+                        d_out_bytes: int, stream: int = 0) -> None:
+    """Compression without any device allocation (fixed in-library scratch,
+    at most 65536 chunks per call); the outcome is in *d_out_bytes."""
+    _check(load().lz_compress_noalloc(d_in, n_bytes, ctypes.byref(p.c()), d_out, out_cap,
+                                      d_out_bytes, stream), "lz_compress_noalloc")
 
 
 def lz_sync(ctx: int, stream: int = 0) -> int:
