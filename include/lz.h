@@ -148,6 +148,52 @@ lz_status lz_compress_noalloc(const void *d_in, uint64_t n_bytes, const lz_param
                               void *d_out, uint64_t out_cap, uint64_t *d_out_bytes,
                               lz_stream_t stream);
 
+/* ---- Batches: many buffers in one persistent launch ------------------------
+ * A batch is planned once on the host (lz_batch_create: validates every item,
+ * uploads per-buffer descriptors, sizes and allocates its own scratch) and
+ * run any number of times (lz_batch_run: a scratch clear and one persistent
+ * kernel whose warps take chunks of all buffers from one work counter; no
+ * host synchronisation, no allocation, so a run can be captured in a CUDA
+ * graph and replayed).  The result of every item is byte-identical to
+ * lz_compress / lz_decompress of that item alone.  Device errors are sticky
+ * in the context, as for the single-buffer calls. */
+typedef struct lz_batch_item {
+  const void *d_in;      /* input (compress) or stream (decompress)         */
+  uint64_t in_bytes;
+  void *d_out;           /* output buffer                                   */
+  uint64_t out_cap;
+  uint64_t *d_out_bytes; /* device uint64, 8-byte aligned: produced size    */
+  lz_params params;      /* compress: this item's parameters; decompress:
+                            ignored (each stream's header is read)          */
+} lz_batch_item;
+
+typedef struct lz_batch lz_batch;
+
+/* Plan a batch of n_items over the host array `items` (decompress != 0: the
+ * items are GLZ1 streams to decompress; their headers are read from the
+ * device, synchronously).  Errors are those of the single-buffer calls
+ * (checked per item) plus LZ_ERR_NOMEM.  The buffers named by the items
+ * must stay valid while the batch is run. */
+lz_status lz_batch_create(lz_ctx *ctx, const lz_batch_item *items, uint32_t n_items,
+                          int decompress, lz_batch **out);
+
+/* Enqueue one run of the batch on `stream`. */
+lz_status lz_batch_run(lz_ctx *ctx, lz_batch *batch, lz_stream_t stream);
+
+/* Free a batch (synchronises its device first). */
+void lz_batch_destroy(lz_batch *batch);
+
+/* Choose chunk_bytes and window for data of `symbol_bytes`-byte symbols from
+ * timed trial compressions of a device-resident sample: among C in {2048,
+ * 4096, 8192} and W in {64, 128, 256}, the fastest whose compression ratio
+ * is within 2% of the best ratio found; min_match 3 (2 for 4-byte symbols),
+ * max_match 255.  The choice changes the stream (it is recorded in its
+ * header), never the arithmetic: the stream is exactly what lz_compress
+ * produces with the chosen parameters.  Synchronous; allocates and frees
+ * temporary device buffers. */
+lz_status lz_autotune(lz_ctx *ctx, const void *d_sample, uint64_t sample_bytes,
+                      uint32_t symbol_bytes, lz_params *out);
+
 /* Synchronise `stream`, then return and clear the context's sticky device
  * error (LZ_OK if none).  When several errors occurred the most severe is
  * returned: INTERNAL, TIMEOUT, CORRUPT, then BUFFER_TOO_SMALL. */

@@ -81,16 +81,17 @@ struct Links {
 // lane groups (only in slabs where such a collision occurs).
 template <int S>
 __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
-                                             uint32_t k, const CompressArgs &A,
-                                             uint16_t *table, uint32_t *maybe,
-                                             const Links &links, uint32_t lane) {
-  const uint32_t H = 1u << A.sm.hash_log2;
+                                             uint32_t k, const BufDesc &A,
+                                             const CompressSmem &sm, uint16_t *table,
+                                             uint32_t *maybe, const Links &links,
+                                             uint32_t lane) {
+  const uint32_t H = 1u << sm.hash_log2;
   uint32_t *t32 = reinterpret_cast<uint32_t *>(table);
   for (uint32_t i = lane; i < H / 2; i += 32) t32[i] = 0xFFFFFFFFu;
   __syncwarp();
 
   const uint32_t g = min(A.m, 8u / S);
-  const uint32_t tshift = 64u - A.sm.hash_log2;
+  const uint32_t tshift = 64u - sm.hash_log2;
   const uint32_t lt = lanemask_lt(lane);
   const uint32_t nslab = (k + 31) / 32;
   constexpr uint32_t kGroup = 4;  // slabs whose hashes are formed together
@@ -194,7 +195,7 @@ constexpr uint32_t kChainWork = 384;
 // Returns false when the work cap stopped the walk with candidates left.
 template <int S>
 __device__ __forceinline__ bool chain_match(const typename SymType<S>::T *sym,
-                                            uint32_t k, const CompressArgs &A,
+                                            uint32_t k, const BufDesc &A,
                                             const Links &links, uint32_t q,
                                             uint32_t &best, uint32_t &bd) {
   const uint32_t lim = min(A.M, k - q);
@@ -231,7 +232,7 @@ __device__ __forceinline__ bool chain_match(const typename SymType<S>::T *sym,
 // left; the longest survives, the smallest offset breaks ties (warp min).
 template <int S, int NJ>
 __device__ __forceinline__ void window_match(const typename SymType<S>::T *sym,
-                                             uint32_t k, const CompressArgs &A,
+                                             uint32_t k, const BufDesc &A,
                                              uint32_t p, uint32_t lane,
                                              uint32_t &L_out, uint32_t &d_out) {
   using Sym = typename SymType<S>::T;
@@ -324,15 +325,15 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x, uint32_t lane,
 // literal runs in parallel.
 template <int S, int NJ>
 __device__ __forceinline__ void greedy_walk(const typename SymType<S>::T *sym,
-                                            uint32_t k, const CompressArgs &A,
-                                            const uint32_t *maybe,
+                                            uint32_t k, const BufDesc &A,
+                                            const CompressSmem &sm, const uint32_t *maybe,
                                             const Links &links, uint8_t *flags,
                                             uint8_t *pay, uint32_t lane,
                                             uint32_t &ntok_out, uint32_t &pay_out,
                                             bool &sane) {
   const uint8_t *in_bytes = reinterpret_cast<const uint8_t *>(sym);
   uint32_t *flag_words = reinterpret_cast<uint32_t *>(flags);
-  const uint32_t pay_cap = A.sm.pay_bytes;
+  const uint32_t pay_cap = sm.pay_bytes;
   sane = true;
   const uint32_t nw = (k + 31) / 32;
   const uint32_t tsz_match = 1 + A.offB;
@@ -542,183 +543,261 @@ __device__ __forceinline__ bool lookback_wait(const unsigned long long *status,
 // Step 5 for a chunk whose global offset is known: publish its inclusive
 // prefix, its index entry (every 64th chunk), the stream size (last chunk)
 // and copy its record (from shared staging or a parking slot).
-__device__ __forceinline__ void place_record(const CompressArgs &A, uint32_t c,
-                                             uint64_t excl, uint64_t rec,
+__device__ __forceinline__ void place_record(const CompressArgs &A, const BufDesc &B,
+                                             uint32_t c, uint64_t excl, uint64_t rec,
                                              const uint8_t *src1, uint32_t n1,
                                              const uint8_t *src2, uint32_t n2,
                                              bool data_ok, uint32_t lane) {
-  publish(A.status, c, kPrefix, excl + rec, lane);
+  publish(A.status + B.gbase, c, kPrefix, excl + rec, lane);
   if (c % kIndexStride == 0) {
-    uint8_t *idx = A.out + kHeaderBytes + static_cast<uint64_t>(kTableEntry) * A.nc +
+    uint8_t *idx = B.out + kHeaderBytes + static_cast<uint64_t>(kTableEntry) * B.nc +
                    8ull * (c / kIndexStride);
     st_le_bytes(idx, excl, 8, lane);
   }
-  const uint64_t dst = A.records_at + excl;
-  if (c + 1 == A.nc && lane == 0) *A.out_bytes = dst + rec;
+  const uint64_t dst = B.records_at + excl;
+  if (c + 1 == B.nc && lane == 0) *B.out_bytes = dst + rec;
   if (!data_ok) return;
-  if (dst + rec > A.cap) {
+  if (dst + rec > B.cap) {
     if (lane == 0) atomicOr(A.err, kErrSmall);
     return;
   }
-  uint8_t *o = A.out + dst;
+  uint8_t *o = B.out + dst;
   warp_copy(o, src1, n1, lane);
   if (n2) warp_copy(o + n1, src2, n2, lane);
 }
 
+__device__ __forceinline__ BufDesc buffer_of(const CompressArgs &A, uint32_t item) {
+  return A.items ? A.items[item] : A.buf;
+}
+
+// A warp's shared-memory slice, TMA barrier phase and parking slots (lane s
+// < park_slots describes slot s: chunk, buffer, record bytes).
+struct WarpState {
+  uint8_t *inb, *flags, *pay, *links_base, *slots;
+  uint32_t *maybe;
+  uint64_t *bar;
+  uint32_t phase;
+  uint32_t slot_c, slot_item, slot_rec;
+};
+
 // Parking slots of this warp whose chunk can now be placed are placed and
 // freed; with `wait`, every occupied slot is placed (blocking).
-__device__ __forceinline__ void drain_parked(const CompressArgs &A, uint8_t *slots,
-                                             uint32_t &slot_c, uint32_t &slot_rec,
+__device__ __forceinline__ void drain_parked(const CompressArgs &A, WarpState &W,
                                              bool wait, uint32_t lane) {
   for (uint32_t sidx = 0; sidx < A.park_slots; ++sidx) {
-    const uint32_t cs = __shfl_sync(kFull, slot_c, sidx);
+    const uint32_t cs = __shfl_sync(kFull, W.slot_c, sidx);
     if (cs == kFreeSlot) continue;
-    const uint32_t rs = __shfl_sync(kFull, slot_rec, sidx);
+    const uint32_t rs = __shfl_sync(kFull, W.slot_rec, sidx);
+    const uint32_t is = __shfl_sync(kFull, W.slot_item, sidx);
+    const BufDesc B = buffer_of(A, is);
     uint64_t excl;
-    bool ok = lookback_try(A.status, cs, lane, excl);
+    bool ok = lookback_try(A.status + B.gbase, cs, lane, excl);
     bool data_ok = true;
     if (!ok && wait) {
       ok = true;
-      data_ok = lookback_wait(A.status, cs, lane, A.err, excl);
+      data_ok = lookback_wait(A.status + B.gbase, cs, lane, A.err, excl);
     }
     if (!ok) continue;
-    const uint8_t *slot = slots + static_cast<uint64_t>(sidx) * A.park_slot_bytes;
-    place_record(A, cs, excl, rs, slot, rs, nullptr, 0, data_ok, lane);
-    if (lane == sidx) slot_c = kFreeSlot;
+    const uint8_t *slot = W.slots + static_cast<uint64_t>(sidx) * A.park_slot_bytes;
+    place_record(A, B, cs, excl, rs, slot, rs, nullptr, 0, data_ok, lane);
+    if (lane == sidx) W.slot_c = kFreeSlot;
     __syncwarp();
   }
 }
 
-template <int S, int NJ>
-__global__ void __launch_bounds__(256) compress_kernel(const CompressArgs A) {
-  using Sym = typename SymType<S>::T;
-  extern __shared__ __align__(128) uint8_t smem[];
-  const uint32_t lane = threadIdx.x & 31;
+__device__ __forceinline__ void init_warp_state(const CompressArgs &A, uint8_t *smem,
+                                                WarpState &W, uint32_t lane) {
   const uint32_t warp = threadIdx.x >> 5;
   uint8_t *ws = smem + warp * A.sm.per_warp;
-  uint8_t *inb = ws + A.sm.in_off;
-  uint8_t *flags = ws + A.sm.flags_off;
-  uint8_t *pay = ws + A.sm.pay_off;
-  uint32_t *maybe = reinterpret_cast<uint32_t *>(ws + A.sm.maybe_off);
-  const Links links{ws + A.sm.prev_off, maybe, A.W > 256};
-  uint64_t *bar = reinterpret_cast<uint64_t *>(ws + A.sm.mbar_off);
-  const Sym *sym = reinterpret_cast<const Sym *>(inb);
-
+  W.inb = ws + A.sm.in_off;
+  W.flags = ws + A.sm.flags_off;
+  W.pay = ws + A.sm.pay_off;
+  W.links_base = ws + A.sm.prev_off;
+  W.maybe = reinterpret_cast<uint32_t *>(ws + A.sm.maybe_off);
+  W.bar = reinterpret_cast<uint64_t *>(ws + A.sm.mbar_off);
   if (lane == 0) {
-    mbar_init(bar, 1);
+    mbar_init(W.bar, 1);
     fence_mbar_init();
   }
   __syncwarp();
-  uint32_t phase = 0;
-  // this warp's parking slots (lane s < park_slots describes slot s)
+  W.phase = 0;
   const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + warp;
-  uint8_t *slots = A.park + gw * A.park_slots * A.park_slot_bytes;
-  uint32_t slot_c = kFreeSlot, slot_rec = 0;
+  W.slots = A.park + gw * A.park_slots * A.park_slot_bytes;
+  W.slot_c = kFreeSlot;
+  W.slot_item = 0;
+  W.slot_rec = 0;
+}
 
-  while (true) {
-    uint32_t c = 0;
-    if (lane == 0) c = atomicAdd(A.ticket, 1u);
-    c = __shfl_sync(kFull, c, 0);
-    if (c >= A.nc) break;
-
-    if (c == 0) {  // header
-      uint32_t b = 0;
-      switch (lane) {
-        case 0: b = 'G'; break;
-        case 1: b = 'L'; break;
-        case 2: b = 'Z'; break;
-        case 3: b = '1'; break;
-        case 4: b = 1; break;
-        case 5: b = A.S; break;
-        case 6: b = A.offB; break;
-        case 7: b = A.m; break;
-        case 8: b = A.M; break;
-        default:
-          if (lane >= 12 && lane < 16) b = A.C >> (8 * (lane - 12));
-          else if (lane >= 16 && lane < 20) b = A.W >> (8 * (lane - 16));
-          else if (lane >= 20 && lane < 24) b = A.nc >> (8 * (lane - 20));
-          else if (lane >= 24) b = static_cast<uint32_t>(A.n >> (8 * (lane - 24)));
-      }
-      A.out[lane] = static_cast<uint8_t>(b);
-    }
-
-    // 1. stage the chunk
-    const uint64_t chunk_at = static_cast<uint64_t>(c) * A.C;
-    const uint32_t bytes =
-        (c + 1 < A.nc) ? A.C : static_cast<uint32_t>(A.n - chunk_at);
-    const uint32_t k = bytes / S;
-    const uint8_t *src = A.in + chunk_at;
-    const uint32_t bulk = A.in_aligned ? (bytes & ~15u) : 0u;
-    if (lane == 0 && A.in_aligned) {
-      // warm L2 for the chunk a wave of warps ahead (whichever warp takes it)
-      const uint64_t ahead = static_cast<uint64_t>(c) + gridDim.x * (blockDim.x >> 5);
-      if (ahead + 1 < A.nc) prefetch_l2(A.in + ahead * A.C, A.C);
-    }
-    if (bulk && lane == 0) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(bar, bulk);
-      bulk_g2s(inb, src, bulk, bar);
-    }
-    for (uint32_t i = bulk + lane; i < bytes; i += 32) inb[i] = src[i];
-    bool staged = true;
-    if (bulk) {
-      staged = mbar_wait_bounded(bar, phase);
-      phase ^= 1u;
-      if (!staged && lane == 0) atomicOr(A.err, kErrTimeout);
-    }
-    __syncwarp();
-
-    // 2. candidate filter (hash table lives in the payload staging area)
-    build_chains<S>(sym, k, A, reinterpret_cast<uint16_t *>(pay), maybe, links, lane);
-    const uint32_t fwords = (k + 31) / 32;
-    for (uint32_t i = lane; i < fwords; i += 32) reinterpret_cast<uint32_t *>(flags)[i] = 0;
-    __syncwarp();
-
-    // 3. greedy parse + local offsets
-    uint32_t ntok, pb;
-    bool sane;
-    greedy_walk<S, NJ>(sym, k, A, maybe, links, flags, pay, lane, ntok, pb, sane);
-    if (!sane && lane == 0) atomicOr(A.err, kErrInternal);
-    const uint32_t fb = (ntok + 7) / 8;
-    const uint64_t rec = static_cast<uint64_t>(fb) + pb;
-
-    // 4. global offset: publish the aggregate at once, so that no other
-    // chunk waits on this warp; place the record now if the offset is
-    // known, else park it and move on (placed after a later chunk)
-    const bool data_ok = staged && sane;
-    if (c != 0) publish(A.status, c, kAgg, rec, lane);
-    uint8_t *tab = A.out + kHeaderBytes + static_cast<uint64_t>(kTableEntry) * c;
-    if (lane < 4)
-      tab[lane] = static_cast<uint8_t>(ntok >> (8 * lane));
-    else if (lane < 8)
-      tab[lane] = static_cast<uint8_t>(pb >> (8 * (lane - 4)));
-    drain_parked(A, slots, slot_c, slot_rec, false, lane);
-    uint64_t excl;
-    if (lookback_try(A.status, c, lane, excl)) {
-      place_record(A, c, excl, rec, flags, fb, pay, pb, data_ok, lane);
-    } else {
-      const uint32_t free_mask =
-          __ballot_sync(kFull, lane < A.park_slots && slot_c == kFreeSlot);
-      if (free_mask && data_ok) {
-        const uint32_t sidx = __ffs(free_mask) - 1;
-        uint8_t *slot = slots + static_cast<uint64_t>(sidx) * A.park_slot_bytes;
-        warp_copy(slot, flags, fb, lane);
-        warp_copy(slot + fb, pay, pb, lane);
-        if (lane == sidx) {
-          slot_c = c;
-          slot_rec = static_cast<uint32_t>(rec);
-        }
-      } else {
-        const bool ok = lookback_wait(A.status, c, lane, A.err, excl);
-        place_record(A, c, excl, rec, flags, fb, pay, pb, data_ok && ok, lane);
-      }
-    }
-    __syncwarp();
-    // a copy that never landed leaves the barrier phase unknown: stop here
-    // (the chunk was still published, so no other warp waits on it)
-    if (!staged) break;
+__device__ __forceinline__ void write_header(const BufDesc &B, uint32_t lane) {
+  uint32_t b = 0;
+  switch (lane) {
+    case 0: b = 'G'; break;
+    case 1: b = 'L'; break;
+    case 2: b = 'Z'; break;
+    case 3: b = '1'; break;
+    case 4: b = 1; break;
+    case 5: b = B.S; break;
+    case 6: b = B.offB; break;
+    case 7: b = B.m; break;
+    case 8: b = B.M; break;
+    default:
+      if (lane >= 12 && lane < 16) b = B.C >> (8 * (lane - 12));
+      else if (lane >= 16 && lane < 20) b = B.W >> (8 * (lane - 16));
+      else if (lane >= 20 && lane < 24) b = B.nc >> (8 * (lane - 20));
+      else if (lane >= 24) b = static_cast<uint32_t>(B.n >> (8 * (lane - 24)));
   }
-  drain_parked(A, slots, slot_c, slot_rec, true, lane);
+  B.out[lane] = static_cast<uint8_t>(b);
+}
+
+// Steps 1-5 for chunk c of buffer B (item `item` of a batch).  Returns false
+// when the TMA copy never landed (the warp must stop: its barrier phase is
+// unknown; the chunk was still published so no other warp waits on it).
+template <int S, int NJ>
+__device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufDesc &B,
+                                               uint32_t item, uint32_t c, WarpState &W,
+                                               uint32_t lane) {
+  using Sym = typename SymType<S>::T;
+  const Sym *sym = reinterpret_cast<const Sym *>(W.inb);
+  const Links links{W.links_base, W.maybe, B.W > 256};
+  unsigned long long *status = A.status + B.gbase;
+  if (c == 0) write_header(B, lane);
+
+  // 1. stage the chunk
+  const uint64_t chunk_at = static_cast<uint64_t>(c) * B.C;
+  const uint32_t bytes = (c + 1 < B.nc) ? B.C : static_cast<uint32_t>(B.n - chunk_at);
+  const uint32_t k = bytes / S;
+  const uint8_t *src = B.in + chunk_at;
+  const uint32_t bulk = B.in_aligned ? (bytes & ~15u) : 0u;
+  if (lane == 0 && B.in_aligned) {
+    // warm L2 for the chunk a wave of warps ahead (whichever warp takes it)
+    const uint64_t ahead = static_cast<uint64_t>(c) + gridDim.x * (blockDim.x >> 5);
+    if (ahead + 1 < B.nc) prefetch_l2(B.in + ahead * B.C, B.C);
+  }
+  if (bulk && lane == 0) {
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(W.bar, bulk);
+    bulk_g2s(W.inb, src, bulk, W.bar);
+  }
+  for (uint32_t i = bulk + lane; i < bytes; i += 32) W.inb[i] = src[i];
+  bool staged = true;
+  if (bulk) {
+    staged = mbar_wait_bounded(W.bar, W.phase);
+    W.phase ^= 1u;
+    if (!staged && lane == 0) atomicOr(A.err, kErrTimeout);
+  }
+  __syncwarp();
+
+  // 2. candidate filter (hash table lives in the payload staging area)
+  build_chains<S>(sym, k, B, A.sm, reinterpret_cast<uint16_t *>(W.pay), W.maybe, links, lane);
+  const uint32_t fwords = (k + 31) / 32;
+  for (uint32_t i = lane; i < fwords; i += 32) reinterpret_cast<uint32_t *>(W.flags)[i] = 0;
+  __syncwarp();
+
+  // 3. greedy parse + local offsets
+  uint32_t ntok, pb;
+  bool sane;
+  greedy_walk<S, NJ>(sym, k, B, A.sm, W.maybe, links, W.flags, W.pay, lane, ntok, pb, sane);
+  if (!sane && lane == 0) atomicOr(A.err, kErrInternal);
+  const uint32_t fb = (ntok + 7) / 8;
+  const uint64_t rec = static_cast<uint64_t>(fb) + pb;
+
+  // 4. global offset: publish the aggregate at once, so that no other
+  // chunk waits on this warp; place the record now if the offset is
+  // known, else park it and move on (placed after a later chunk)
+  const bool data_ok = staged && sane;
+  if (c != 0) publish(status, c, kAgg, rec, lane);
+  uint8_t *tab = B.out + kHeaderBytes + static_cast<uint64_t>(kTableEntry) * c;
+  if (lane < 4)
+    tab[lane] = static_cast<uint8_t>(ntok >> (8 * lane));
+  else if (lane < 8)
+    tab[lane] = static_cast<uint8_t>(pb >> (8 * (lane - 4)));
+  drain_parked(A, W, false, lane);
+  uint64_t excl;
+  if (lookback_try(status, c, lane, excl)) {
+    place_record(A, B, c, excl, rec, W.flags, fb, W.pay, pb, data_ok, lane);
+  } else {
+    const uint32_t free_mask =
+        __ballot_sync(kFull, lane < A.park_slots && W.slot_c == kFreeSlot);
+    if (free_mask && data_ok) {
+      const uint32_t sidx = __ffs(free_mask) - 1;
+      uint8_t *slot = W.slots + static_cast<uint64_t>(sidx) * A.park_slot_bytes;
+      warp_copy(slot, W.flags, fb, lane);
+      warp_copy(slot + fb, W.pay, pb, lane);
+      if (lane == sidx) {
+        W.slot_c = c;
+        W.slot_item = item;
+        W.slot_rec = static_cast<uint32_t>(rec);
+      }
+    } else {
+      const bool ok = lookback_wait(status, c, lane, A.err, excl);
+      place_record(A, B, c, excl, rec, W.flags, fb, W.pay, pb, data_ok && ok, lane);
+    }
+  }
+  __syncwarp();
+  return staged;
+}
+
+__device__ __forceinline__ uint32_t take_ticket(uint32_t *ticket, uint32_t lane) {
+  uint32_t t = 0;
+  if (lane == 0) t = atomicAdd(ticket, 1u);
+  return __shfl_sync(kFull, t, 0);
+}
+
+// Single buffer: the symbol size is a template parameter.
+template <int S, int NJ>
+__global__ void __launch_bounds__(256) compress_kernel(const CompressArgs A) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const uint32_t lane = threadIdx.x & 31;
+  WarpState W;
+  init_warp_state(A, smem, W, lane);
+  while (true) {
+    const uint32_t c = take_ticket(A.ticket, lane);
+    if (c >= A.buf.nc) break;
+    if (!compress_chunk<S, NJ>(A, A.buf, 0, c, W, lane)) break;
+  }
+  drain_parked(A, W, true, lane);
+}
+
+// Buffer holding global chunk g: the last item whose first chunk is <= g,
+// found by a 32-way search (one probe per lane per round).
+__device__ __forceinline__ uint32_t find_item(const CompressArgs &A, uint64_t g,
+                                              uint32_t lane) {
+  uint32_t lo = 0, hi = A.n_items;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    const uint32_t step = (hi - lo + 31) / 32;
+    const uint32_t idx = lo + lane * step;
+    const bool le = idx < hi && A.item_base[idx] <= g;
+    const uint32_t cnt = __popc(__ballot_sync(kFull, le));  // >= 1: lane 0 probes lo
+    const uint32_t nlo = lo + (cnt - 1) * step;
+    hi = min(hi, nlo + step);
+    lo = nlo;
+  }
+  return lo;
+}
+
+// Batch: work items are the chunks of all buffers in order; each buffer
+// carries its own parameters, so the symbol size is dispatched per chunk.
+template <int NJ>
+__global__ void __launch_bounds__(256) compress_batch_kernel(const CompressArgs A) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const uint32_t lane = threadIdx.x & 31;
+  WarpState W;
+  init_warp_state(A, smem, W, lane);
+  while (true) {
+    const uint32_t g = take_ticket(A.ticket, lane);
+    if (g >= A.total_chunks) break;
+    const uint32_t item = find_item(A, g, lane);
+    const BufDesc B = A.items[item];
+    const uint32_t c = static_cast<uint32_t>(g - B.gbase);
+    bool ok;
+    switch (B.S) {
+      case 1: ok = compress_chunk<1, NJ>(A, B, item, c, W, lane); break;
+      case 2: ok = compress_chunk<2, NJ>(A, B, item, c, W, lane); break;
+      default: ok = compress_chunk<4, NJ>(A, B, item, c, W, lane); break;
+    }
+    if (!ok) break;
+  }
+  drain_parked(A, W, true, lane);
 }
 
 }  // namespace glz

@@ -357,6 +357,110 @@ __global__ void __launch_bounds__(256) decompress_kernel(const DecompressArgs A)
     if (!decode_chunk(A, h, c, records_at, ring, rmask, win, bar, phase, lane)) break;
 }
 
+// Batched decompression: chunks of all streams in order, grid-stride; each
+// warp finds its stream by a 32-way search over the streams' first chunks.
+__global__ void __launch_bounds__(256) decompress_batch_kernel(const DecompressBatchArgs B) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warp = threadIdx.x >> 5;
+  const uint32_t wpb = blockDim.x >> 5;
+  if (blockIdx.x == 0) {  // zero-byte streams: check the header, size 0
+    for (uint32_t i = threadIdx.x; i < B.n_empty; i += blockDim.x) {
+      Header h;
+      if (!read_header(B.empties[i].in, h) || h.n != 0) atomicOr(B.err, kErrCorrupt);
+      *B.empties[i].out_bytes = 0;
+    }
+  }
+  const uint64_t need = 16 + 4ull * B.ring_n + B.win_bytes;
+  const uint64_t fit = B.smem_bytes / need;
+  const uint32_t active = fit < wpb ? static_cast<uint32_t>(fit) : wpb;
+  if (warp >= active) return;
+  uint8_t *ws = smem + warp * need;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(ws);
+  uint32_t *ring = reinterpret_cast<uint32_t *>(ws + 16);
+  uint8_t *win = ws + 16 + 4ull * B.ring_n;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  uint32_t phase = 0;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * active;
+  for (uint64_t g = static_cast<uint64_t>(blockIdx.x) * active + warp; g < B.total_chunks;
+       g += stride) {
+    uint32_t lo = 0, hi = B.n_items;
+    while (hi - lo > 1) {
+      const uint32_t step = (hi - lo + 31) / 32;
+      const uint32_t idx = lo + lane * step;
+      const bool le = idx < hi && B.item_base[idx] <= g;
+      const uint32_t cnt = __popc(__ballot_sync(kFull, le));
+      const uint32_t nlo = lo + (cnt - 1) * step;
+      hi = min(hi, nlo + step);
+      lo = nlo;
+    }
+    const DecItem it = B.items[lo];
+    const uint32_t c = static_cast<uint32_t>(g - it.gbase);
+    Header h{};
+    const bool ok = it.in_bytes >= kHeaderBytes && read_header(it.in, h);
+    const uint64_t records_at = kHeaderBytes + 8ull * h.nc +
+                                8ull * ((h.nc + kIndexStride - 1) / kIndexStride);
+    uint32_t ring_need = 64;
+    while (ring_need < h.W + 32) ring_need <<= 1;
+    // the header must still be the one the plan sized the slices for
+    const bool fits = ok && h.nc == it.nc && ring_need <= B.ring_n &&
+                      record_bound(h.C / h.S, h) + 32 <= B.win_bytes &&
+                      records_at <= it.in_bytes && h.n <= it.out_cap;
+    if (!fits) {
+      if (lane == 0) atomicOr(B.err, h.n > it.out_cap && ok ? kErrSmall : kErrCorrupt);
+      continue;
+    }
+    if (c == 0 && lane == 0) *it.out_bytes = h.n;
+    DecompressArgs A{};
+    A.in = it.in;
+    A.in_bytes = it.in_bytes;
+    A.out = it.out;
+    A.out_cap = it.out_cap;
+    A.out_bytes = it.out_bytes;
+    A.err = B.err;
+    A.out_aligned = static_cast<int>(it.out_aligned);
+    if (!decode_chunk(A, h, c, records_at, ring, B.ring_n - 1, win, bar, phase, lane)) break;
+  }
+}
+
+cudaError_t launch_decompress_batch(DecompressBatchArgs B, int block, cudaStream_t stream) {
+  static std::mutex mu;
+  static int per_sm = 0, sms = 0, cached_block = -1;
+  static uint32_t cached_smem = 0;
+  const size_t smem = B.smem_bytes;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (cached_block != block || cached_smem != B.smem_bytes) {
+      cudaError_t e = cudaFuncSetAttribute(decompress_batch_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(smem));
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decompress_batch_kernel,
+                                                        block, smem);
+      if (e != cudaSuccess) return e;
+      int dev = 0;
+      e = cudaGetDevice(&dev);
+      if (e != cudaSuccess) return e;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
+      cached_block = block;
+      cached_smem = B.smem_bytes;
+    }
+  }
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const uint64_t warps = block / 32;
+  uint64_t want = (B.total_chunks + warps - 1) / warps;
+  if (want == 0) want = 1;
+  const uint64_t cap = static_cast<uint64_t>(per_sm) * sms;
+  const unsigned grid = static_cast<unsigned>(want < cap ? want : cap);
+  decompress_batch_kernel<<<grid, block, smem, stream>>>(B);
+  return cudaGetLastError();
+}
+
 // Shared memory per block; each warp takes a slice sized from the header.
 constexpr uint32_t kDecodeSmemPerBlock = 72 * 1024;
 

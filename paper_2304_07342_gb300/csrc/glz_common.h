@@ -36,7 +36,8 @@ struct CompressSmem {
   uint32_t hash_log2;  // hash table entries = 1 << hash_log2 (u16 each)
 };
 
-struct CompressArgs {
+// One buffer to compress (one stream): per-buffer parameters and places.
+struct BufDesc {
   const uint8_t *in;
   uint64_t n;
   uint8_t *out;
@@ -44,10 +45,19 @@ struct CompressArgs {
   unsigned long long *out_bytes;
   uint32_t S, C, W, m, M, offB;
   uint32_t nc;          // chunks
+  uint32_t in_aligned;  // in is 16-byte aligned: TMA bulk staging
   uint64_t records_at;  // byte offset of the records region
-  int in_aligned;       // in is 16-byte aligned: TMA bulk staging
-  CompressSmem sm;
-  unsigned long long *status;  // nc look-back words (cleared per call)
+  uint64_t gbase;       // index of this buffer's chunk 0 among all chunks
+};
+
+struct CompressArgs {
+  BufDesc buf;                 // single-buffer launch
+  const BufDesc *items;        // batched launch (nullptr for a single buffer)
+  const uint64_t *item_base;   // items[i].gbase, ascending (batched launch)
+  uint32_t n_items;            // non-empty items
+  uint64_t total_chunks;       // chunks over all items
+  CompressSmem sm;             // per-warp layout (covers every item)
+  unsigned long long *status;  // one look-back word per chunk (cleared per call)
   uint32_t *ticket;            // work counter (cleared per call)
   uint32_t *err;               // sticky error bits
   uint8_t *park;               // parking slots: grid warps x park_slots
@@ -64,6 +74,31 @@ struct DecompressArgs {
   uint32_t *err;
   uint32_t smem_bytes;  // dynamic shared memory per block
   int out_aligned;      // out is 16-byte aligned
+};
+
+// One stream of a batched decompression.
+struct DecItem {
+  const uint8_t *in;
+  uint64_t in_bytes;
+  uint8_t *out;
+  uint64_t out_cap;
+  unsigned long long *out_bytes;
+  uint64_t gbase;  // index of this stream's chunk 0 among all chunks
+  uint32_t nc;
+  uint32_t out_aligned;
+};
+
+struct DecompressBatchArgs {
+  const DecItem *items;        // streams with at least one chunk
+  const uint64_t *item_base;   // items[i].gbase, ascending
+  uint32_t n_items;
+  uint64_t total_chunks;
+  const DecItem *empties;      // streams of zero bytes
+  uint32_t n_empty;
+  uint32_t ring_n;             // ring entries per warp (>= W + 32 for every stream)
+  uint32_t win_bytes;          // record window per warp (>= every record + 32)
+  uint32_t smem_bytes;         // dynamic shared memory per block
+  uint32_t *err;
 };
 
 }  // namespace glz

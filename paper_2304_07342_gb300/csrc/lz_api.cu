@@ -5,7 +5,10 @@
 
 #include <cstdint>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
+#include <new>
+#include <vector>
 
 #include "../../include/lz.h"
 #include "glz_common.h"
@@ -18,6 +21,20 @@ cudaError_t launch_compress_s2(const CompressArgs &A, uint32_t nj, int block,
 cudaError_t launch_compress_s4(const CompressArgs &A, uint32_t nj, int block,
                                unsigned grid, cudaStream_t stream);
 cudaError_t launch_decompress(DecompressArgs A, int block, cudaStream_t stream);
+cudaError_t launch_compress_batch(const CompressArgs &A, const BufDesc *empties,
+                                  uint32_t n_empty, uint32_t nj, int block, unsigned grid,
+                                  cudaStream_t stream);
+cudaError_t launch_decompress_batch(DecompressBatchArgs B, int block, cudaStream_t stream);
+
+// Gather the 32-byte headers of n streams into one device array.
+__global__ void gather_headers(const uint8_t *const *ins, const uint64_t *in_bytes,
+                               uint32_t n, uint8_t *hdr) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n * 32;
+       i += gridDim.x * blockDim.x) {
+    const uint32_t item = i / 32, b = i % 32;
+    hdr[i] = in_bytes[item] >= 32 ? ins[item][b] : 0;
+  }
+}
 
 // Empty input: the stream is the header alone (n_chunks = 0, n_bytes = 0).
 __global__ void header_kernel(uint8_t *out, uint32_t S, uint32_t offB,
@@ -276,20 +293,22 @@ lz_status lz_compress(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
   if (e != cudaSuccess) return LZ_ERR_CUDA;
 
   glz::CompressArgs A{};
-  A.in = static_cast<const uint8_t *>(d_in);
-  A.n = n_bytes;
-  A.out = static_cast<uint8_t *>(d_out);
-  A.cap = out_cap;
-  A.out_bytes = out_bytes;
-  A.S = S;
-  A.C = C;
-  A.W = p->window;
-  A.m = p->min_match;
-  A.M = p->max_match;
-  A.offB = offB;
-  A.nc = static_cast<uint32_t>(nc);
-  A.records_at = records_at;
-  A.in_aligned = (reinterpret_cast<uintptr_t>(d_in) % 16) == 0;
+  A.buf.in = static_cast<const uint8_t *>(d_in);
+  A.buf.n = n_bytes;
+  A.buf.out = static_cast<uint8_t *>(d_out);
+  A.buf.cap = out_cap;
+  A.buf.out_bytes = out_bytes;
+  A.buf.S = S;
+  A.buf.C = C;
+  A.buf.W = p->window;
+  A.buf.m = p->min_match;
+  A.buf.M = p->max_match;
+  A.buf.offB = offB;
+  A.buf.nc = static_cast<uint32_t>(nc);
+  A.buf.records_at = records_at;
+  A.buf.in_aligned = (reinterpret_cast<uintptr_t>(d_in) % 16) == 0;
+  A.buf.gbase = 0;
+  A.total_chunks = nc;
   A.sm = sm;
   A.park = static_cast<uint8_t *>(ctx->scratch) + park_at;
   A.park_slots = kParkSlots;
@@ -490,20 +509,22 @@ extern "C" lz_status lz_compress_noalloc(const void *d_in, uint64_t n_bytes,
       cudaMemsetAsync(nd->scratch, 0, 4, st) != cudaSuccess)
     return LZ_ERR_CUDA;
   glz::CompressArgs A{};
-  A.in = static_cast<const uint8_t *>(d_in);
-  A.n = n_bytes;
-  A.out = static_cast<uint8_t *>(d_out);
-  A.cap = out_cap;
-  A.out_bytes = out_bytes;
-  A.S = S;
-  A.C = C;
-  A.W = p->window;
-  A.m = p->min_match;
-  A.M = p->max_match;
-  A.offB = offB;
-  A.nc = static_cast<uint32_t>(nc);
-  A.records_at = records_at;
-  A.in_aligned = (reinterpret_cast<uintptr_t>(d_in) % 16) == 0;
+  A.buf.in = static_cast<const uint8_t *>(d_in);
+  A.buf.n = n_bytes;
+  A.buf.out = static_cast<uint8_t *>(d_out);
+  A.buf.cap = out_cap;
+  A.buf.out_bytes = out_bytes;
+  A.buf.S = S;
+  A.buf.C = C;
+  A.buf.W = p->window;
+  A.buf.m = p->min_match;
+  A.buf.M = p->max_match;
+  A.buf.offB = offB;
+  A.buf.nc = static_cast<uint32_t>(nc);
+  A.buf.records_at = records_at;
+  A.buf.in_aligned = (reinterpret_cast<uintptr_t>(d_in) % 16) == 0;
+  A.buf.gbase = 0;
+  A.total_chunks = nc;
   A.sm = sm;
   A.park = nullptr;  // no parking slots: blocking look-back
   A.park_slots = 0;
@@ -524,3 +545,386 @@ extern "C" lz_status lz_compress_noalloc(const void *d_in, uint64_t n_bytes,
   noalloc_report<<<1, 32, 0, st>>>(A.err, out_bytes);
   return cuda_status(cudaGetLastError());
 }
+
+// ---------------------------------------------------------------------------
+// Batches: many buffers in one persistent launch.
+
+struct lz_batch {
+  int decompress = 0;
+  int device = 0;
+  std::vector<void *> owned;  // device allocations owned by the batch
+  // compression
+  glz::CompressArgs cargs{};
+  const glz::BufDesc *d_empty = nullptr;
+  uint32_t n_empty = 0, nj = 1;
+  int block = 32;
+  unsigned grid = 1;
+  size_t clear_bytes = 0;
+  void *scratch = nullptr;
+  // decompression
+  glz::DecompressBatchArgs dargs{};
+  int dblock = 256;
+};
+
+namespace {
+
+lz_status batch_alloc(lz_batch *b, size_t bytes, void **p) {
+  *p = nullptr;
+  if (bytes == 0) return LZ_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) return cuda_status(e);
+  b->owned.push_back(*p);
+  return LZ_OK;
+}
+
+template <typename T>
+lz_status batch_upload(lz_batch *b, const std::vector<T> &v, const T **dst) {
+  void *p = nullptr;
+  lz_status s = batch_alloc(b, v.size() * sizeof(T), &p);
+  if (s != LZ_OK) return s;
+  if (!v.empty() && cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) !=
+                        cudaSuccess)
+    return LZ_ERR_CUDA;
+  *dst = static_cast<const T *>(p);
+  return LZ_OK;
+}
+
+// Per-warp slice covering every parameter set of a batch: each region at its
+// largest size.
+glz::CompressSmem compress_layout_max(const std::vector<lz_params> &ps) {
+  uint64_t in = 16, links = 16, flags = 16, pay = 16, maybe = 16;
+  for (const lz_params &p : ps) {
+    const glz::CompressSmem one = compress_layout(&p);
+    in = std::max<uint64_t>(in, one.prev_off - one.in_off);
+    links = std::max<uint64_t>(links, one.flags_off - one.prev_off);
+    flags = std::max<uint64_t>(flags, one.pay_off - one.flags_off);
+    pay = std::max<uint64_t>(pay, one.pay_bytes);
+    maybe = std::max<uint64_t>(maybe, one.mbar_off - one.maybe_off);
+  }
+  glz::CompressSmem sm{};
+  uint32_t at = 0;
+  sm.in_off = at;
+  at += static_cast<uint32_t>(in);
+  sm.prev_off = at;
+  at += static_cast<uint32_t>(links);
+  sm.flags_off = at;
+  at += static_cast<uint32_t>(flags);
+  sm.pay_off = at;
+  sm.pay_bytes = static_cast<uint32_t>(pay);
+  at += static_cast<uint32_t>(pay);
+  sm.maybe_off = at;
+  at += static_cast<uint32_t>(maybe);
+  sm.mbar_off = at;
+  at += 16;
+  sm.per_warp = (at + 127) & ~127u;
+  uint32_t lg = 1;
+  while (lg < 15 && (2u << (lg + 1)) <= sm.pay_bytes) ++lg;
+  sm.hash_log2 = lg;
+  return sm;
+}
+
+lz_status batch_create_compress(lz_ctx *ctx, const lz_batch_item *items, uint32_t n,
+                                lz_batch *b) {
+  std::vector<glz::BufDesc> descs, empties;
+  std::vector<uint64_t> bases;
+  std::vector<lz_params> ps;
+  uint64_t total = 0, kmax = 1;
+  uint32_t nj = 1;
+  for (uint32_t i = 0; i < n; ++i) {
+    const lz_batch_item &it = items[i];
+    const lz_params *p = &it.params;
+    if (!params_ok(p) || !it.d_out || !it.d_out_bytes) return LZ_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(it.d_out_bytes) % 8 != 0) return LZ_ERR_INVALID_ARG;
+    if (it.in_bytes > 0 && !it.d_in) return LZ_ERR_INVALID_ARG;
+    if (it.in_bytes % p->symbol_bytes != 0) return LZ_ERR_INVALID_ARG;
+    const uint64_t nc = div_up(it.in_bytes, p->chunk_bytes);
+    if (nc > 0xFFFFFFFFull) return LZ_ERR_INVALID_ARG;
+    const uint64_t records_at = glz::kHeaderBytes + glz::kTableEntry * nc +
+                                8ull * div_up(nc, glz::kIndexStride);
+    if (it.out_cap < records_at) return LZ_ERR_BUFFER_TOO_SMALL;
+    glz::BufDesc d{};
+    d.in = static_cast<const uint8_t *>(it.d_in);
+    d.n = it.in_bytes;
+    d.out = static_cast<uint8_t *>(it.d_out);
+    d.cap = it.out_cap;
+    d.out_bytes = reinterpret_cast<unsigned long long *>(it.d_out_bytes);
+    d.S = p->symbol_bytes;
+    d.C = p->chunk_bytes;
+    d.W = p->window;
+    d.m = p->min_match;
+    d.M = p->max_match;
+    d.offB = off_bytes(p->window);
+    d.nc = static_cast<uint32_t>(nc);
+    d.in_aligned = (reinterpret_cast<uintptr_t>(it.d_in) % 16) == 0;
+    d.records_at = records_at;
+    d.gbase = total;
+    if (nc == 0) {
+      empties.push_back(d);
+      continue;
+    }
+    descs.push_back(d);
+    bases.push_back(total);
+    total += nc;
+    ps.push_back(*p);
+    kmax = std::max<uint64_t>(kmax, p->chunk_bytes / p->symbol_bytes);
+    uint32_t j = 1;
+    while (32 * j < p->window) j *= 2;
+    nj = std::max(nj, j);
+  }
+  glz::CompressSmem sm = ps.empty() ? glz::CompressSmem{} : compress_layout_max(ps);
+  if (!ps.empty() && static_cast<int64_t>(sm.per_warp) > ctx->smem_optin)
+    return LZ_ERR_INVALID_ARG;
+  int block = 32;
+  int64_t best_warps = 0, best_blocks = 1;
+  for (int wpb = 1; !ps.empty() && wpb <= kCompressWarps; wpb *= 2) {
+    const int64_t per_block = static_cast<int64_t>(sm.per_warp) * wpb + ctx->smem_reserved;
+    if (per_block - ctx->smem_reserved > ctx->smem_optin) break;
+    int64_t blocks = ctx->smem_per_sm / per_block;
+    if (blocks > 32) blocks = 32;
+    if (blocks * wpb > best_warps) {
+      best_warps = blocks * wpb;
+      best_blocks = blocks;
+      block = 32 * wpb;
+    }
+  }
+  const uint64_t wpb = block / 32;
+  uint64_t grid = std::max<uint64_t>(1, div_up(total, wpb));
+  if (grid > static_cast<uint64_t>(best_blocks) * ctx->sms) grid = best_blocks * ctx->sms;
+  const uint32_t slot_bytes = round16(div_up(kmax, 8) + sm.pay_bytes + 16);
+  const size_t status_end = kScratchHead + 8ull * total;
+  const size_t park_at = (status_end + 255) & ~static_cast<size_t>(255);
+  const size_t scratch = park_at + static_cast<size_t>(slot_bytes) * kParkSlots * wpb * grid;
+  lz_status s = batch_alloc(b, scratch, &b->scratch);
+  if (s != LZ_OK) return s;
+  const glz::BufDesc *d_items = nullptr, *d_empty = nullptr;
+  const uint64_t *d_base = nullptr;
+  if ((s = batch_upload(b, descs, &d_items)) != LZ_OK) return s;
+  if ((s = batch_upload(b, bases, &d_base)) != LZ_OK) return s;
+  if ((s = batch_upload(b, empties, &d_empty)) != LZ_OK) return s;
+  glz::CompressArgs &A = b->cargs;
+  A.items = d_items;
+  A.item_base = d_base;
+  A.n_items = static_cast<uint32_t>(descs.size());
+  A.total_chunks = total;
+  A.sm = sm;
+  A.ticket = static_cast<uint32_t *>(b->scratch);
+  A.status = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(b->scratch) +
+                                                     kScratchHead);
+  A.err = ctx->d_err;
+  A.park = static_cast<uint8_t *>(b->scratch) + park_at;
+  A.park_slots = kParkSlots;
+  A.park_slot_bytes = slot_bytes;
+  b->d_empty = d_empty;
+  b->n_empty = static_cast<uint32_t>(empties.size());
+  b->nj = nj;
+  b->block = block;
+  b->grid = static_cast<unsigned>(grid);
+  b->clear_bytes = status_end;
+  return LZ_OK;
+}
+
+uint64_t header_u(const uint8_t *h, int at, int n) {
+  uint64_t v = 0;
+  for (int i = 0; i < n; ++i) v |= static_cast<uint64_t>(h[at + i]) << (8 * i);
+  return v;
+}
+
+lz_status batch_create_decompress(lz_ctx *ctx, const lz_batch_item *items, uint32_t n,
+                                  lz_batch *b) {
+  std::vector<const uint8_t *> ins(n);
+  std::vector<uint64_t> in_bytes(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!items[i].d_in || !items[i].d_out_bytes) return LZ_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(items[i].d_out_bytes) % 8 != 0) return LZ_ERR_INVALID_ARG;
+    if (items[i].in_bytes < glz::kHeaderBytes) return LZ_ERR_CORRUPT;
+    ins[i] = static_cast<const uint8_t *>(items[i].d_in);
+    in_bytes[i] = items[i].in_bytes;
+  }
+  std::vector<uint8_t> hdr(static_cast<size_t>(n) * 32);
+  {
+    const uint8_t *const *d_ins = nullptr;
+    const uint64_t *d_inb = nullptr;
+    lz_status s;
+    if ((s = batch_upload(b, ins, &d_ins)) != LZ_OK) return s;
+    if ((s = batch_upload(b, in_bytes, &d_inb)) != LZ_OK) return s;
+    void *d_hdr = nullptr;
+    if ((s = batch_alloc(b, hdr.size(), &d_hdr)) != LZ_OK) return s;
+    if (n) {
+      glz::gather_headers<<<std::min<uint32_t>(1024, (n * 32 + 255) / 256), 256>>>(
+          d_ins, d_inb, n, static_cast<uint8_t *>(d_hdr));
+      if (cudaMemcpy(hdr.data(), d_hdr, hdr.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return LZ_ERR_CUDA;
+    }
+  }
+  std::vector<glz::DecItem> descs, empties;
+  std::vector<uint64_t> bases;
+  uint64_t total = 0, max_rec = 0;
+  uint32_t max_w = 1;
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint8_t *h = &hdr[static_cast<size_t>(i) * 32];
+    lz_params p{h[5], static_cast<uint32_t>(header_u(h, 12, 4)),
+                static_cast<uint32_t>(header_u(h, 16, 4)), h[7], h[8]};
+    const uint64_t nn = header_u(h, 24, 8);
+    const uint64_t nc = header_u(h, 20, 4);
+    if (std::memcmp(h, "GLZ1", 4) != 0 || h[4] != 1 || h[9] || h[10] || h[11] ||
+        !params_ok(&p) || h[6] != off_bytes(p.window) || nn % p.symbol_bytes != 0 ||
+        nc != div_up(nn, p.chunk_bytes))
+      return LZ_ERR_CORRUPT;
+    if (items[i].out_cap < nn || (nn > 0 && !items[i].d_out)) return LZ_ERR_BUFFER_TOO_SMALL;
+    glz::DecItem d{};
+    d.in = ins[i];
+    d.in_bytes = in_bytes[i];
+    d.out = static_cast<uint8_t *>(items[i].d_out);
+    d.out_cap = items[i].out_cap;
+    d.out_bytes = reinterpret_cast<unsigned long long *>(items[i].d_out_bytes);
+    d.nc = static_cast<uint32_t>(nc);
+    d.out_aligned = (reinterpret_cast<uintptr_t>(items[i].d_out) % 16) == 0;
+    d.gbase = total;
+    if (nc == 0) {
+      empties.push_back(d);
+      continue;
+    }
+    descs.push_back(d);
+    bases.push_back(total);
+    total += nc;
+    max_w = std::max(max_w, p.window);
+    max_rec = std::max(max_rec, record_bound(p.chunk_bytes / p.symbol_bytes, p.symbol_bytes,
+                                             off_bytes(p.window), p.min_match));
+  }
+  uint32_t ring_n = 64;
+  while (ring_n < max_w + 32) ring_n <<= 1;
+  const uint32_t win = round16(max_rec + 32);
+  const uint64_t need = 16 + 4ull * ring_n + win;
+  if (static_cast<int64_t>(need) > ctx->smem_optin) return LZ_ERR_INVALID_ARG;
+  const uint64_t warps = std::min<uint64_t>(8, ctx->smem_optin / need);
+  const glz::DecItem *d_items = nullptr, *d_empty = nullptr;
+  const uint64_t *d_base = nullptr;
+  lz_status s;
+  if ((s = batch_upload(b, descs, &d_items)) != LZ_OK) return s;
+  if ((s = batch_upload(b, bases, &d_base)) != LZ_OK) return s;
+  if ((s = batch_upload(b, empties, &d_empty)) != LZ_OK) return s;
+  glz::DecompressBatchArgs &B = b->dargs;
+  B.items = d_items;
+  B.item_base = d_base;
+  B.n_items = static_cast<uint32_t>(descs.size());
+  B.total_chunks = total;
+  B.empties = d_empty;
+  B.n_empty = static_cast<uint32_t>(empties.size());
+  B.ring_n = ring_n;
+  B.win_bytes = win;
+  B.smem_bytes = static_cast<uint32_t>(need * warps);
+  B.err = ctx->d_err;
+  b->dblock = static_cast<int>(32 * warps);
+  return LZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lz_status lz_batch_create(lz_ctx *ctx, const lz_batch_item *items, uint32_t n_items,
+                          int decompress, lz_batch **out) {
+  if (!ctx || !out || (n_items > 0 && !items)) return LZ_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
+  lz_batch *b = new (std::nothrow) lz_batch();
+  if (!b) return LZ_ERR_NOMEM;
+  b->decompress = decompress ? 1 : 0;
+  b->device = ctx->device;
+  lz_status s = decompress ? batch_create_decompress(ctx, items, n_items, b)
+                           : batch_create_compress(ctx, items, n_items, b);
+  if (s != LZ_OK) {
+    for (void *p : b->owned) cudaFree(p);
+    delete b;
+    return s;
+  }
+  *out = b;
+  return LZ_OK;
+}
+
+lz_status lz_batch_run(lz_ctx *ctx, lz_batch *b, lz_stream_t stream) {
+  if (!ctx || !b || b->device != ctx->device) return LZ_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (b->decompress) {
+    if (b->dargs.total_chunks == 0 && b->dargs.n_empty == 0) return LZ_OK;
+    b->dargs.err = ctx->d_err;
+    return cuda_status(glz::launch_decompress_batch(b->dargs, b->dblock, st));
+  }
+  b->cargs.err = ctx->d_err;
+  if (b->clear_bytes && cudaMemsetAsync(b->scratch, 0, b->clear_bytes, st) != cudaSuccess)
+    return LZ_ERR_CUDA;
+  return cuda_status(glz::launch_compress_batch(b->cargs, b->d_empty, b->n_empty, b->nj,
+                                                b->block, b->grid, st));
+}
+
+void lz_batch_destroy(lz_batch *b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  for (void *p : b->owned) cudaFree(p);
+  delete b;
+}
+
+lz_status lz_autotune(lz_ctx *ctx, const void *d_sample, uint64_t sample_bytes,
+                      uint32_t symbol_bytes, lz_params *out) {
+  if (!ctx || !d_sample || !out) return LZ_ERR_INVALID_ARG;
+  if (symbol_bytes != 1 && symbol_bytes != 2 && symbol_bytes != 4) return LZ_ERR_INVALID_ARG;
+  sample_bytes -= sample_bytes % symbol_bytes;
+  if (sample_bytes == 0) return LZ_ERR_INVALID_ARG;
+  const uint32_t Cs[3] = {2048, 4096, 8192};
+  const uint32_t Ws[3] = {64, 128, 256};
+  const uint32_t m = symbol_bytes == 4 ? 2u : 3u;
+  struct Trial {
+    lz_params p;
+    double ratio, seconds;
+  };
+  std::vector<Trial> trials;
+  uint64_t cap = 0;
+  for (uint32_t C : Cs)
+    for (uint32_t W : Ws) {
+      lz_params p{symbol_bytes, C, W, m, 255};
+      cap = std::max(cap, lz_compressed_bound(sample_bytes, &p));
+      trials.push_back({p, 0.0, 0.0});
+    }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
+  void *d_out = nullptr, *d_nb = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  lz_status s = LZ_OK;
+  if (cudaMalloc(&d_out, cap) != cudaSuccess || cudaMalloc(&d_nb, 8) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    s = LZ_ERR_NOMEM;
+  for (Trial &t : trials) {
+    if (s != LZ_OK) break;
+    for (int rep = 0; rep < 3 && s == LZ_OK; ++rep) {  // first run warms up
+      cudaEventRecord(e0, nullptr);
+      s = lz_compress(ctx, d_sample, sample_bytes, &t.p, d_out, cap,
+                      static_cast<uint64_t *>(d_nb), nullptr);
+      cudaEventRecord(e1, nullptr);
+      if (s == LZ_OK) s = lz_sync(ctx, nullptr);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) t.seconds += ms * 1e-3 / 2;
+    }
+    uint64_t size = 0;
+    if (s == LZ_OK && cudaMemcpy(&size, d_nb, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      s = LZ_ERR_CUDA;
+    t.ratio = size ? static_cast<double>(sample_bytes) / size : 0.0;
+  }
+  if (s == LZ_OK) {
+    // the fastest set whose ratio is within 2% of the best ratio seen
+    double best_ratio = 0;
+    for (const Trial &t : trials) best_ratio = std::max(best_ratio, t.ratio);
+    const Trial *pick = nullptr;
+    for (const Trial &t : trials)
+      if (t.ratio >= 0.98 * best_ratio && (!pick || t.seconds < pick->seconds)) pick = &t;
+    *out = pick->p;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (d_out) cudaFree(d_out);
+  if (d_nb) cudaFree(d_nb);
+  return s;
+}
+
+}  // extern "C"

@@ -31,7 +31,8 @@ _NAMES = {0: "LZ_OK", 1: "LZ_ERR_INVALID_ARG", 2: "LZ_ERR_BUFFER_TOO_SMALL",
 # every symbol include/lz.h declares
 EXPORTS = ("lz_create", "lz_destroy", "lz_status_string", "lz_check_params",
            "lz_compressed_bound", "lz_compress", "lz_decompressed_size",
-           "lz_decompress", "lz_sync", "lz_compress_noalloc")
+           "lz_decompress", "lz_sync", "lz_compress_noalloc", "lz_batch_create",
+           "lz_batch_run", "lz_batch_destroy", "lz_autotune")
 
 
 class LzError(RuntimeError):
@@ -44,6 +45,12 @@ class lz_params(ctypes.Structure):
     _fields_ = [("symbol_bytes", ctypes.c_uint32), ("chunk_bytes", ctypes.c_uint32),
                 ("window", ctypes.c_uint32), ("min_match", ctypes.c_uint32),
                 ("max_match", ctypes.c_uint32)]
+
+
+class lz_batch_item(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_void_p), ("in_bytes", ctypes.c_uint64),
+                ("d_out", ctypes.c_void_p), ("out_cap", ctypes.c_uint64),
+                ("d_out_bytes", ctypes.c_void_p), ("params", lz_params)]
 
 
 @dataclass(frozen=True)
@@ -93,6 +100,15 @@ def load(path: str = LIB_PATH):
     lib.lz_sync.restype = i32
     lib.lz_compress_noalloc.argtypes = [vp, u64, pp, vp, u64, vp, vp]
     lib.lz_compress_noalloc.restype = i32
+    lib.lz_batch_create.argtypes = [vp, ctypes.POINTER(lz_batch_item), ctypes.c_uint32, i32,
+                                    ctypes.POINTER(vp)]
+    lib.lz_batch_create.restype = i32
+    lib.lz_batch_run.argtypes = [vp, vp, vp]
+    lib.lz_batch_run.restype = i32
+    lib.lz_batch_destroy.argtypes = [vp]
+    lib.lz_batch_destroy.restype = None
+    lib.lz_autotune.argtypes = [vp, vp, u64, ctypes.c_uint32, pp]
+    lib.lz_autotune.restype = i32
     _lib = lib
     return lib
 
@@ -151,6 +167,34 @@ def lz_compress_noalloc(d_in: int, n_bytes: int, p: Params, d_out: int, out_cap:
     at most 65536 chunks per call); the outcome is in *d_out_bytes."""
     _check(load().lz_compress_noalloc(d_in, n_bytes, ctypes.byref(p.c()), d_out, out_cap,
                                       d_out_bytes, stream), "lz_compress_noalloc")
+
+
+def lz_batch_create(ctx: int, items, decompress: bool = False) -> int:
+    """Plan a batch; `items` is a list of (d_in, in_bytes, d_out, out_cap,
+    d_out_bytes, Params-or-None) tuples of raw device pointers."""
+    arr = (lz_batch_item * max(1, len(items)))()
+    for i, (din, nin, dout, cap, dnb, p) in enumerate(items):
+        arr[i] = lz_batch_item(din, nin, dout, cap, dnb,
+                               p.c() if p is not None else lz_params(0, 0, 0, 0, 0))
+    h = ctypes.c_void_p()
+    _check(load().lz_batch_create(ctx, arr, len(items), 1 if decompress else 0,
+                                  ctypes.byref(h)), "lz_batch_create")
+    return h.value
+
+
+def lz_batch_run(ctx: int, batch: int, stream: int = 0) -> None:
+    _check(load().lz_batch_run(ctx, batch, stream), "lz_batch_run")
+
+
+def lz_batch_destroy(batch: int) -> None:
+    load().lz_batch_destroy(batch)
+
+
+def lz_autotune(ctx: int, d_sample: int, sample_bytes: int, symbol_bytes: int) -> Params:
+    out = lz_params()
+    _check(load().lz_autotune(ctx, d_sample, sample_bytes, symbol_bytes, ctypes.byref(out)),
+           "lz_autotune")
+    return Params(out.symbol_bytes, out.chunk_bytes, out.window, out.min_match, out.max_match)
 
 
 def lz_sync(ctx: int, stream: int = 0) -> int:

@@ -26,7 +26,7 @@ def sha256(a: np.ndarray) -> str:
 
 
 def _block_rngs(seed: int, n: int):
-    nblk = max(1, math.ceil(n / _BLOCK))
+    nblk = math.ceil(n / _BLOCK)
     seqs = np.random.SeedSequence(seed).spawn(nblk)
     for i, s in enumerate(seqs):
         lo = i * _BLOCK
