@@ -56,6 +56,10 @@ def _workloads():
             ("float32 field 64x512x256", lambda r: synth.gaussian_field((64, 512, 256), seed=r),
              (4, 8192, 256, 2, 255)),
         ],
+        "field-256MiB": [
+            ("float32 field 512x512x256", lambda r: synth.gaussian_field(seed=r),
+             (4, 8192, 256, 2, 255)),
+        ],
         "markov16-64MiB": [
             ("uint16 markov codes 32Mi", lambda r: synth.markov_codes(32 << 20, seed=r).astype(np.uint16),
              (2, 4096, 128, 3, 255)),
@@ -276,7 +280,49 @@ def run_gpu(args):
         line["cpu_baseline"] = _cpu_baseline(args, hosts=[it["host"] for it in items])
     if world > 1:
         dist.destroy_process_group()
+        return line
+    # the two patterns built on the same kernels, each against plain launches
+    for it in items:
+        for k in ("d_in", "d_out", "d_dec"):
+            it[k] = None
+    torch.cuda.empty_cache()
+    if args.batched:
+        line["batched"] = _batched(torch, codec, args)
+    if args.served > 0:
+        line["served"] = _served(torch, codec, args, args.served)
     return line
+
+
+def _batched(torch, codec, args, n_buffers: int = 10_000):
+    """Many uneven buffers: one persistent launch under a CUDA graph vs one
+    plain launch per buffer (compress and decompress of every buffer)."""
+    from paper_2304_07342_gb300 import batch
+    t = time.perf_counter()
+    w = batch.build(torch, n_buffers=n_buffers, seed=args.seed, autotune_codec=codec)
+    build_s = time.perf_counter() - t
+    r = batch.run(torch, codec, w, steps=3)
+    r.update({"workload": f"{n_buffers} buffers, log-uniform 4 KiB-16 MiB, 4 kinds",
+              "setup_seconds": round(build_s, 2),
+              "speedup_vs_per_buffer": round(r["compress_batched_gbs"] /
+                                             r["compress_per_buffer_gbs"], 3)})
+    del w
+    torch.cuda.empty_cache()
+    return r
+
+
+def _served(torch, codec, args, seconds: float, budget: int = 40 * 10 ** 9):
+    """Poisson request stream: continuous batching vs one plain launch per
+    request, same trace, same HBM budget."""
+    from paper_2304_07342_gb300 import serve
+    tr = serve.build_trace(torch, codec, rate=2000.0, duration=seconds, seed=args.seed)
+    b = serve.run_batched(torch, codec, tr, budget_bytes=budget)
+    torch.cuda.empty_cache()
+    p = serve.run_plain(torch, codec, tr, budget_bytes=budget)
+    tr = None
+    torch.cuda.empty_cache()
+    return {"workload": f"2000 req/s Poisson for {seconds:g} s, 70% compress, "
+                        "lognormal(256 KiB, 1.5) sizes capped at 64 MiB, S in {1,2,4}",
+            "budget_bytes": budget, "batched": b, "plain": p}
 
 
 def _e2e(codec, items, stream, args):
@@ -368,6 +414,10 @@ def main():
     ap.add_argument("--workload", default="field+indices")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the 10,000-buffer batched comparison")
+    ap.add_argument("--served", type=float, default=10.0,
+                    help="seconds of the serving trace (0 skips it; the full trace is 60)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -171,17 +171,21 @@ typedef struct lz_batch lz_batch;
 
 /* Plan a batch of n_items over the host array `items` (decompress != 0: the
  * items are GLZ1 streams to decompress; their headers are read from the
- * device, synchronously).  Errors are those of the single-buffer calls
- * (checked per item) plus LZ_ERR_NOMEM.  The buffers named by the items
- * must stay valid while the batch is run. */
+ * device, which synchronises `stream`).  The batch's device memory is
+ * allocated stream-ordered on `stream` (cudaMallocAsync) and its descriptors
+ * uploaded on it, so no device-wide synchronisation happens; runs must be
+ * ordered after this call (same stream, or an event).  Errors are those of
+ * the single-buffer calls (checked per item) plus LZ_ERR_NOMEM.  The buffers
+ * named by the items must stay valid while the batch is run. */
 lz_status lz_batch_create(lz_ctx *ctx, const lz_batch_item *items, uint32_t n_items,
-                          int decompress, lz_batch **out);
+                          int decompress, lz_stream_t stream, lz_batch **out);
 
 /* Enqueue one run of the batch on `stream`. */
 lz_status lz_batch_run(lz_ctx *ctx, lz_batch *batch, lz_stream_t stream);
 
-/* Free a batch (synchronises its device first). */
-void lz_batch_destroy(lz_batch *batch);
+/* Free a batch: its device memory is released stream-ordered on `stream`
+ * (after the work already enqueued there); the handle is gone at once. */
+void lz_batch_destroy(lz_batch *batch, lz_stream_t stream);
 
 /* Choose chunk_bytes and window for data of `symbol_bytes`-byte symbols from
  * timed trial compressions of a device-resident sample: among C in {2048,
@@ -193,6 +197,33 @@ void lz_batch_destroy(lz_batch *batch);
  * temporary device buffers. */
 lz_status lz_autotune(lz_ctx *ctx, const void *d_sample, uint64_t sample_bytes,
                       uint32_t symbol_bytes, lz_params *out);
+
+/* Stitch one shard stream into a whole-input stream.  Chunks are
+ * independent (section 3.3.1), so the stream of bytes [b0, b1) of an input
+ * holds exactly the chunk records the whole-input stream holds for those
+ * chunks when b0 is a multiple of 64 * chunk_bytes (one index superblock):
+ * shards compressed separately (on several GPUs, or one after another) can
+ * be placed side by side.  The one exchange between shards is the
+ * exclusive scan of their (chunk count, record bytes); given it,
+ *   d_shard, shard_bytes  the shard's GLZ1 stream (device, 8-byte aligned);
+ *   shard_chunks          its chunk count (must equal its header's);
+ *   chunk_base            chunks before it (a multiple of 64);
+ *   total_chunks, total_bytes  the whole input's chunk and byte counts;
+ *   record_base           record bytes of all earlier shards;
+ *   d_out, out_cap        the whole-input stream (device, 8-byte aligned);
+ * this call writes the shard's table entries, index entries (rebased by
+ * record_base) and records at their places in d_out, and the header too
+ * when chunk_base is 0.  Once every shard has been stitched, d_out holds
+ * exactly the stream lz_compress writes for the whole input.  Argument and
+ * range errors are returned synchronously; a shard header that disagrees
+ * with the arguments (magic, version, chunk count, chunk count of
+ * total_bytes) is LZ_ERR_CORRUPT from lz_sync and nothing is written.
+ * The paper has no multi-GPU path: this is its chunk independence used
+ * across shards. */
+lz_status lz_stitch(lz_ctx *ctx, const void *d_shard, uint64_t shard_bytes,
+                    uint64_t shard_chunks, uint64_t chunk_base, uint64_t total_chunks,
+                    uint64_t total_bytes, uint64_t record_base, void *d_out,
+                    uint64_t out_cap, lz_stream_t stream);
 
 /* Synchronise `stream`, then return and clear the context's sticky device
  * error (LZ_OK if none).  When several errors occurred the most severe is

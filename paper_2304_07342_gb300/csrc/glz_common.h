@@ -65,6 +65,21 @@ struct CompressArgs {
   uint32_t park_slot_bytes;    // one worst-case record, 16-byte multiple
 };
 
+// Placement of one shard stream inside a whole-input stream (lz_stitch).
+struct StitchArgs {
+  const uint8_t *shard;   // 8-byte aligned
+  uint64_t shard_chunks;  // chunks in the shard
+  uint64_t chunk_base;    // chunks before it (multiple of kIndexStride)
+  uint64_t total_chunks;
+  uint64_t total_bytes;
+  uint64_t record_base;   // record bytes of the shards before it
+  uint64_t src_records;   // byte offset of the shard's records
+  uint64_t record_bytes;  // the shard's record bytes
+  uint64_t dst_records;   // byte offset of this shard's records in out
+  uint8_t *out;           // 8-byte aligned
+  uint32_t *err;
+};
+
 struct DecompressArgs {
   const uint8_t *in;
   uint64_t in_bytes;

@@ -25,6 +25,7 @@ cudaError_t launch_compress_batch(const CompressArgs &A, const BufDesc *empties,
                                   uint32_t n_empty, uint32_t nj, int block, unsigned grid,
                                   cudaStream_t stream);
 cudaError_t launch_decompress_batch(DecompressBatchArgs B, int block, cudaStream_t stream);
+cudaError_t launch_stitch(const StitchArgs &A, int sms, cudaStream_t stream);
 
 // Gather the 32-byte headers of n streams into one device array.
 __global__ void gather_headers(const uint8_t *const *ins, const uint64_t *in_bytes,
@@ -373,6 +374,45 @@ lz_status lz_decompress(lz_ctx *ctx, const void *d_in, uint64_t in_bytes,
                                             reinterpret_cast<cudaStream_t>(stream)));
 }
 
+lz_status lz_stitch(lz_ctx *ctx, const void *d_shard, uint64_t shard_bytes,
+                    uint64_t shard_chunks, uint64_t chunk_base, uint64_t total_chunks,
+                    uint64_t total_bytes, uint64_t record_base, void *d_out,
+                    uint64_t out_cap, lz_stream_t stream) {
+  if (!ctx || !d_shard || !d_out) return LZ_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(d_shard) % 8 != 0 ||
+      reinterpret_cast<uintptr_t>(d_out) % 8 != 0)
+    return LZ_ERR_INVALID_ARG;
+  if (total_chunks > 0xFFFFFFFFull || shard_chunks > total_chunks ||
+      chunk_base > total_chunks - shard_chunks)
+    return LZ_ERR_INVALID_ARG;
+  if (shard_chunks > 0 && chunk_base % glz::kIndexStride != 0) return LZ_ERR_INVALID_ARG;
+  const uint64_t src_records = glz::kHeaderBytes + glz::kTableEntry * shard_chunks +
+                               8ull * div_up(shard_chunks, glz::kIndexStride);
+  if (shard_bytes < src_records) return LZ_ERR_INVALID_ARG;
+  const uint64_t records_at = glz::kHeaderBytes + glz::kTableEntry * total_chunks +
+                              8ull * div_up(total_chunks, glz::kIndexStride);
+  const uint64_t record_bytes = shard_bytes - src_records;
+  if (out_cap < records_at || record_base > out_cap - records_at ||
+      record_bytes > out_cap - records_at - record_base)
+    return LZ_ERR_BUFFER_TOO_SMALL;
+  glz::StitchArgs A{};
+  A.shard = static_cast<const uint8_t *>(d_shard);
+  A.shard_chunks = shard_chunks;
+  A.chunk_base = chunk_base;
+  A.total_chunks = total_chunks;
+  A.total_bytes = total_bytes;
+  A.record_base = record_base;
+  A.src_records = src_records;
+  A.record_bytes = record_bytes;
+  A.dst_records = records_at + record_base;
+  A.out = static_cast<uint8_t *>(d_out);
+  A.err = ctx->d_err;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
+  return cuda_status(
+      glz::launch_stitch(A, ctx->sms, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 lz_status lz_sync(lz_ctx *ctx, lz_stream_t stream) {
   if (!ctx) return LZ_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -552,7 +592,8 @@ extern "C" lz_status lz_compress_noalloc(const void *d_in, uint64_t n_bytes,
 struct lz_batch {
   int decompress = 0;
   int device = 0;
-  std::vector<void *> owned;  // device allocations owned by the batch
+  cudaStream_t stream = nullptr;  // allocations and uploads are ordered on it
+  std::vector<void *> owned;      // device allocations owned by the batch
   // compression
   glz::CompressArgs cargs{};
   const glz::BufDesc *d_empty = nullptr;
@@ -568,22 +609,24 @@ struct lz_batch {
 
 namespace {
 
+// Stream-ordered allocation on the batch's stream (no device-wide sync).
 lz_status batch_alloc(lz_batch *b, size_t bytes, void **p) {
   *p = nullptr;
   if (bytes == 0) return LZ_OK;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = cudaMallocAsync(p, bytes, b->stream);
   if (e != cudaSuccess) return cuda_status(e);
   b->owned.push_back(*p);
   return LZ_OK;
 }
 
+// Upload a host array (pageable: the call returns once the data is staged).
 template <typename T>
 lz_status batch_upload(lz_batch *b, const std::vector<T> &v, const T **dst) {
   void *p = nullptr;
   lz_status s = batch_alloc(b, v.size() * sizeof(T), &p);
   if (s != LZ_OK) return s;
-  if (!v.empty() && cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) !=
-                        cudaSuccess)
+  if (!v.empty() && cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T),
+                                    cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
     return LZ_ERR_CUDA;
   *dst = static_cast<const T *>(p);
   return LZ_OK;
@@ -750,9 +793,11 @@ lz_status batch_create_decompress(lz_ctx *ctx, const lz_batch_item *items, uint3
     void *d_hdr = nullptr;
     if ((s = batch_alloc(b, hdr.size(), &d_hdr)) != LZ_OK) return s;
     if (n) {
-      glz::gather_headers<<<std::min<uint32_t>(1024, (n * 32 + 255) / 256), 256>>>(
-          d_ins, d_inb, n, static_cast<uint8_t *>(d_hdr));
-      if (cudaMemcpy(hdr.data(), d_hdr, hdr.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      glz::gather_headers<<<std::min<uint32_t>(1024, (n * 32 + 255) / 256), 256, 0,
+                            b->stream>>>(d_ins, d_inb, n, static_cast<uint8_t *>(d_hdr));
+      if (cudaMemcpyAsync(hdr.data(), d_hdr, hdr.size(), cudaMemcpyDeviceToHost,
+                          b->stream) != cudaSuccess ||
+          cudaStreamSynchronize(b->stream) != cudaSuccess)
         return LZ_ERR_CUDA;
     }
   }
@@ -823,7 +868,7 @@ lz_status batch_create_decompress(lz_ctx *ctx, const lz_batch_item *items, uint3
 extern "C" {
 
 lz_status lz_batch_create(lz_ctx *ctx, const lz_batch_item *items, uint32_t n_items,
-                          int decompress, lz_batch **out) {
+                          int decompress, lz_stream_t stream, lz_batch **out) {
   if (!ctx || !out || (n_items > 0 && !items)) return LZ_ERR_INVALID_ARG;
   *out = nullptr;
   std::lock_guard<std::mutex> lock(ctx->mu);
@@ -832,10 +877,11 @@ lz_status lz_batch_create(lz_ctx *ctx, const lz_batch_item *items, uint32_t n_it
   if (!b) return LZ_ERR_NOMEM;
   b->decompress = decompress ? 1 : 0;
   b->device = ctx->device;
+  b->stream = reinterpret_cast<cudaStream_t>(stream);
   lz_status s = decompress ? batch_create_decompress(ctx, items, n_items, b)
                            : batch_create_compress(ctx, items, n_items, b);
   if (s != LZ_OK) {
-    for (void *p : b->owned) cudaFree(p);
+    for (void *p : b->owned) cudaFreeAsync(p, b->stream);
     delete b;
     return s;
   }
@@ -858,11 +904,11 @@ lz_status lz_batch_run(lz_ctx *ctx, lz_batch *b, lz_stream_t stream) {
                                                 b->block, b->grid, st));
 }
 
-void lz_batch_destroy(lz_batch *b) {
+void lz_batch_destroy(lz_batch *b, lz_stream_t stream) {
   if (!b) return;
   cudaSetDevice(b->device);
-  cudaDeviceSynchronize();
-  for (void *p : b->owned) cudaFree(p);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  for (void *p : b->owned) cudaFreeAsync(p, st);
   delete b;
 }
 

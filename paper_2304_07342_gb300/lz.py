@@ -32,7 +32,7 @@ _NAMES = {0: "LZ_OK", 1: "LZ_ERR_INVALID_ARG", 2: "LZ_ERR_BUFFER_TOO_SMALL",
 EXPORTS = ("lz_create", "lz_destroy", "lz_status_string", "lz_check_params",
            "lz_compressed_bound", "lz_compress", "lz_decompressed_size",
            "lz_decompress", "lz_sync", "lz_compress_noalloc", "lz_batch_create",
-           "lz_batch_run", "lz_batch_destroy", "lz_autotune")
+           "lz_batch_run", "lz_batch_destroy", "lz_autotune", "lz_stitch")
 
 
 class LzError(RuntimeError):
@@ -101,14 +101,16 @@ def load(path: str = LIB_PATH):
     lib.lz_compress_noalloc.argtypes = [vp, u64, pp, vp, u64, vp, vp]
     lib.lz_compress_noalloc.restype = i32
     lib.lz_batch_create.argtypes = [vp, ctypes.POINTER(lz_batch_item), ctypes.c_uint32, i32,
-                                    ctypes.POINTER(vp)]
+                                    vp, ctypes.POINTER(vp)]
     lib.lz_batch_create.restype = i32
     lib.lz_batch_run.argtypes = [vp, vp, vp]
     lib.lz_batch_run.restype = i32
-    lib.lz_batch_destroy.argtypes = [vp]
+    lib.lz_batch_destroy.argtypes = [vp, vp]
     lib.lz_batch_destroy.restype = None
     lib.lz_autotune.argtypes = [vp, vp, u64, ctypes.c_uint32, pp]
     lib.lz_autotune.restype = i32
+    lib.lz_stitch.argtypes = [vp, vp, u64, u64, u64, u64, u64, u64, vp, u64, vp]
+    lib.lz_stitch.restype = i32
     _lib = lib
     return lib
 
@@ -161,6 +163,14 @@ def lz_decompress(ctx: int, d_in: int, in_bytes: int, d_out: int, out_cap: int,
                                 d_out_bytes, stream), "lz_decompress")
 
 
+def lz_stitch(ctx: int, d_shard: int, shard_bytes: int, shard_chunks: int, chunk_base: int,
+              total_chunks: int, total_bytes: int, record_base: int, d_out: int, out_cap: int,
+              stream: int = 0) -> None:
+    """Place one shard stream inside the whole-input stream at d_out."""
+    _check(load().lz_stitch(ctx, d_shard, shard_bytes, shard_chunks, chunk_base, total_chunks,
+                            total_bytes, record_base, d_out, out_cap, stream), "lz_stitch")
+
+
 def lz_compress_noalloc(d_in: int, n_bytes: int, p: Params, d_out: int, out_cap: int,
                         d_out_bytes: int, stream: int = 0) -> None:
     """Compression without any device allocation (fixed in-library scratch,
@@ -169,7 +179,7 @@ def lz_compress_noalloc(d_in: int, n_bytes: int, p: Params, d_out: int, out_cap:
                                       d_out_bytes, stream), "lz_compress_noalloc")
 
 
-def lz_batch_create(ctx: int, items, decompress: bool = False) -> int:
+def lz_batch_create(ctx: int, items, decompress: bool = False, stream: int = 0) -> int:
     """Plan a batch; `items` is a list of (d_in, in_bytes, d_out, out_cap,
     d_out_bytes, Params-or-None) tuples of raw device pointers."""
     arr = (lz_batch_item * max(1, len(items)))()
@@ -177,7 +187,7 @@ def lz_batch_create(ctx: int, items, decompress: bool = False) -> int:
         arr[i] = lz_batch_item(din, nin, dout, cap, dnb,
                                p.c() if p is not None else lz_params(0, 0, 0, 0, 0))
     h = ctypes.c_void_p()
-    _check(load().lz_batch_create(ctx, arr, len(items), 1 if decompress else 0,
+    _check(load().lz_batch_create(ctx, arr, len(items), 1 if decompress else 0, stream,
                                   ctypes.byref(h)), "lz_batch_create")
     return h.value
 
@@ -186,8 +196,8 @@ def lz_batch_run(ctx: int, batch: int, stream: int = 0) -> None:
     _check(load().lz_batch_run(ctx, batch, stream), "lz_batch_run")
 
 
-def lz_batch_destroy(batch: int) -> None:
-    load().lz_batch_destroy(batch)
+def lz_batch_destroy(batch: int, stream: int = 0) -> None:
+    load().lz_batch_destroy(batch, stream)
 
 
 def lz_autotune(ctx: int, d_sample: int, sample_bytes: int, symbol_bytes: int) -> Params:

@@ -60,6 +60,7 @@ def _run_batch(codec, items):
         ins.append(d); outs.append(o); nbs.append(nb)
         desc.append((d.data_ptr() if x.nbytes else 0, x.nbytes, o.data_ptr(), cap, nb.data_ptr(), P))
     b = lz.lz_batch_create(codec.ctx, desc)
+    torch.cuda.synchronize()  # plan uploads done before runs on any stream
     return b, ins, outs, nbs
 
 
@@ -129,6 +130,7 @@ def test_batch_graph_capture_replay(codec):
                 assert int(nb.item()) == r.numel()
                 assert torch.equal(o[: r.numel()], r)
     finally:
+        torch.cuda.synchronize()
         lz.lz_batch_destroy(b)
 
 
