@@ -49,19 +49,19 @@ struct SymType<4> {
 constexpr uint16_t kNoPos = 0xFFFF;  // chunk positions are < 32768
 
 // Chain links: distance from a position to the previous one with the same
-// key hash, 0 if there is none within the window.  One byte per position
-// while W <= 256, two bytes beyond.
-// The stored value is distance - 1; whether a position has a link at all
-// is its bit in the `maybe` mask, so one byte covers windows up to 256.
+// key hash.  One byte per position while W <= 256 (two bytes beyond),
+// holding distance - 1; a position without a link within the window holds
+// all ones, read as distance 256 (or 65536).  A walk only starts at a
+// position that has a link (a marked one), and after its first hop any step
+// of 256 or more leaves the window (W <= 256 for one-byte links), so the
+// sentinel and a true link of 256 both end the walk where they should.
 struct Links {
   uint8_t *base;
-  const uint32_t *has;  // the `maybe` mask
   bool wide;
   __device__ __forceinline__ uint32_t get(uint32_t p) const {
-    if (!((has[p >> 5] >> (p & 31)) & 1u)) return 0;
     return 1u + (wide ? reinterpret_cast<const uint16_t *>(base)[p] : base[p]);
   }
-  __device__ __forceinline__ void set(uint32_t p, uint32_t d) const {  // d >= 1
+  __device__ __forceinline__ void set(uint32_t p, uint32_t d) const {  // 0: none
     if (wide)
       reinterpret_cast<uint16_t *>(base)[p] = static_cast<uint16_t>(d - 1);
     else
@@ -72,13 +72,22 @@ struct Links {
 // Step 2: hash chains.  For every position p with room for m symbols, the
 // key is its first g = min(m, 8/S) symbols; the link of p is the distance to
 // the last earlier position with the same key hash when that lies within
-// the window, and bit p of `maybe` is set when there is such a link.  A
-// match of >= m symbols at p from offset d needs p - d to carry the same
-// key, so every such offset is on p's chain, and an unmarked p has none:
-// skipping unmarked positions as literals leaves the greedy parse
-// unchanged.  The table holds the last position per hash; positions of one
-// 32-position slab that share a hash are linked through __match_any_sync
-// lane groups (only in slabs where such a collision occurs).
+// the window.  A match of >= m symbols at p from offset d needs p - d to
+// carry the same key, so every such offset is on p's chain.
+// Bit p of `maybe` marks the positions whose chain can hold such an offset:
+// p has a link to q, and either q carries p's key or q's own chain goes on
+// within the window (a position with p's key behind q is on q's chain, at
+// most W back from p).  Unmarked positions have no offset with p's key in
+// the window, so skipping them as literals leaves the greedy parse
+// unchanged; the test drops most positions that only share a hash.
+//
+// The table holds the last position of each hash.  Slabs of 32 positions
+// go through it in order: each lane reads its bucket, then all lanes write
+// their position and read it back; a lane that finds another position lost
+// a collision, so its slab holds two positions with one hash.  Only such
+// slabs need the lane groups of __match_any_sync (a shared unit with low
+// throughput).  The key filter runs after four slabs have been linked, on
+// independent loads.
 template <int S>
 __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
                                              uint32_t k, const BufDesc &A,
@@ -94,10 +103,10 @@ __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
   const uint32_t tshift = 64u - sm.hash_log2;
   const uint32_t lt = lanemask_lt(lane);
   const uint32_t nslab = (k + 31) / 32;
-  constexpr uint32_t kGroup = 4;  // slabs whose hashes are formed together
+  constexpr uint32_t kGroup = 4;  // slabs whose hashes and filters are formed together
   for (uint32_t s0 = 0; s0 < nslab; s0 += kGroup) {
-    // independent part for kGroup slabs: keys and hashes
-    uint32_t hh[kGroup];
+    uint32_t hh[kGroup], qq[kGroup], dd[kGroup];
+    uint64_t kk[kGroup];
     bool okk[kGroup];
 #pragma unroll
     for (uint32_t u = 0; u < kGroup; ++u) {
@@ -110,17 +119,17 @@ __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
           if (i < g) key |= static_cast<uint64_t>(sym[p + i]) << (8 * S * i);
       }
       hh[u] = static_cast<uint32_t>((key * 0x9E3779B97F4A7C15ull) >> tshift);
+      kk[u] = key;
       okk[u] = ok;
     }
-    // serial part: the table carries the last position of each hash.  Each
-    // lane reads its bucket, then all lanes write their position and read
-    // it back: a lane that finds another position lost a collision, so its
-    // slab holds two positions with one hash.  Only such slabs need the
-    // lane groups of __match_any_sync (a shared unit with low throughput).
+    // links, slab after slab
 #pragma unroll
     for (uint32_t u = 0; u < kGroup; ++u) {
-      if (s0 + u >= nslab) break;
-      const uint32_t p = (s0 + u) * 32 + lane;
+      qq[u] = kNoPos;
+      dd[u] = 0;
+      if (s0 + u >= nslab) continue;
+      const uint32_t base = (s0 + u) * 32;
+      const uint32_t p = base + lane;
       const bool ok = okk[u];
       const uint32_t h = hh[u];
       const uint32_t old = ok ? table[h] : kNoPos;
@@ -132,16 +141,39 @@ __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
       if (__any_sync(kFull, lost)) {
         const uint32_t grp = __match_any_sync(kFull, ok ? h : (0x10000u + lane));
         const uint32_t lower = grp & lt;
-        if (lower) q = (s0 + u) * 32 + (31u - __clz(lower));
+        if (lower) q = base + (31u - __clz(lower));
         __syncwarp();
         if (ok && (grp >> lane) == 1u) table[h] = static_cast<uint16_t>(p);  // last wins
       }
       const uint32_t dist = (ok && q != kNoPos && p - q <= A.W) ? p - q : 0u;
-      if (dist) links.set(p, dist);
-      const uint32_t bits = __ballot_sync(kFull, dist != 0);
-      if (lane == 0) maybe[s0 + u] = bits;
-      __syncwarp();
+      if (p < k) links.set(p, dist);
+      qq[u] = q;
+      dd[u] = dist;
     }
+    __syncwarp();
+    // candidate filter: q's key, else whether q's chain goes on in reach
+#pragma unroll
+    for (uint32_t u = 0; u < kGroup; ++u) {
+      const uint32_t base = (s0 + u) * 32;
+      const uint32_t q = qq[u], dist = dd[u];
+      const uint32_t dq_slab = __shfl_sync(kFull, dist, (q - base) & 31u);
+      bool mb = false;
+      if (dist) {
+        uint64_t kq = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < 8u / S; ++i)
+          if (i < g) kq |= static_cast<uint64_t>(sym[q + i]) << (8 * S * i);
+        if (kq == kk[u]) {
+          mb = true;
+        } else {
+          const uint32_t dq = q >= base ? dq_slab : links.get(q);
+          mb = dq != 0 && dist + dq <= A.W;
+        }
+      }
+      const uint32_t mbits = __ballot_sync(kFull, mb);
+      if (lane == 0 && s0 + u < nslab) maybe[s0 + u] = mbits;
+    }
+    __syncwarp();
   }
 }
 
@@ -658,7 +690,7 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
                                                uint32_t lane) {
   using Sym = typename SymType<S>::T;
   const Sym *sym = reinterpret_cast<const Sym *>(W.inb);
-  const Links links{W.links_base, W.maybe, B.W > 256};
+  const Links links{W.links_base, B.W > 256};
   unsigned long long *status = A.status + B.gbase;
   if (c == 0) write_header(B, lane);
 

@@ -28,7 +28,7 @@ struct CompressSmem {
   uint32_t in_off;     // staged chunk, C bytes
   uint32_t prev_off;   // u16 per position: previous position, same key hash
   uint32_t flags_off;  // flag bits of up to k tokens
-  uint32_t pay_off;    // payload staging (worst case); also hash table
+  uint32_t pay_off;    // payload staging (worst case); also the hash table
   uint32_t pay_bytes;  // size of the payload staging region
   uint32_t maybe_off;  // one bit per position: a match of >= m may exist
   uint32_t mbar_off;   // mbarrier for the TMA bulk copy

@@ -113,10 +113,14 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(
 // Warp copy of n bytes between any two addresses (shared or global): the
 // destination is written in aligned 32-bit words, each assembled from two
 // aligned source words with a funnel shift; unaligned head and tail bytes
-// are copied singly.  May read up to 3 bytes past the source range (the
-// callers' source regions have that slack).
+// are copied singly.  Eight words per lane are loaded before any is stored,
+// so a copy from global memory waits on one round trip per 1 KiB rather
+// than per 128 bytes.  May read up to 3 bytes past the source range (the
+// callers' source regions have that slack).  Source and destination must
+// not overlap.
 __device__ __forceinline__ void warp_copy(uint8_t *dst, const uint8_t *src,
                                           uint32_t n, uint32_t lane) {
+  constexpr uint32_t U = 8;
   const uint32_t head =
       min(n, (4u - static_cast<uint32_t>(reinterpret_cast<uintptr_t>(dst) & 3u)) & 3u);
   if (lane < head) dst[lane] = src[lane];
@@ -126,12 +130,29 @@ __device__ __forceinline__ void warp_copy(uint8_t *dst, const uint8_t *src,
     const uint32_t sm = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(sb) & 3u);
     const uint32_t *s32 = reinterpret_cast<const uint32_t *>(sb - sm);
     uint32_t *d32 = reinterpret_cast<uint32_t *>(dst + head);
+    uint32_t j = lane;
     if (sm == 0) {
-      for (uint32_t j = lane; j < words; j += 32) d32[j] = s32[j];
+      for (; j + 32 * (U - 1) < words; j += 32 * U) {
+        uint32_t v[U];
+#pragma unroll
+        for (uint32_t i = 0; i < U; ++i) v[i] = s32[j + 32 * i];
+#pragma unroll
+        for (uint32_t i = 0; i < U; ++i) d32[j + 32 * i] = v[i];
+      }
+      for (; j < words; j += 32) d32[j] = s32[j];
     } else {
       const uint32_t sh = 8u * sm;
-      for (uint32_t j = lane; j < words; j += 32)
-        d32[j] = __funnelshift_r(s32[j], s32[j + 1], sh);
+      for (; j + 32 * (U - 1) < words; j += 32 * U) {
+        uint32_t lo[U], hi[U];
+#pragma unroll
+        for (uint32_t i = 0; i < U; ++i) {
+          lo[i] = s32[j + 32 * i];
+          hi[i] = s32[j + 32 * i + 1];
+        }
+#pragma unroll
+        for (uint32_t i = 0; i < U; ++i) d32[j + 32 * i] = __funnelshift_r(lo[i], hi[i], sh);
+      }
+      for (; j < words; j += 32) d32[j] = __funnelshift_r(s32[j], s32[j + 1], sh);
     }
   }
   const uint32_t done = head + 4u * words;
