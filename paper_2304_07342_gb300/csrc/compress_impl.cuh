@@ -55,19 +55,37 @@ constexpr uint16_t kNoPos = 0xFFFF;  // chunk positions are < 32768
 // position that has a link (a marked one), and after its first hop any step
 // of 256 or more leaves the window (W <= 256 for one-byte links), so the
 // sentinel and a true link of 256 both end the walk where they should.
+template <bool WIDE>
 struct Links {
   uint8_t *base;
-  bool wide;
   __device__ __forceinline__ uint32_t get(uint32_t p) const {
-    return 1u + (wide ? reinterpret_cast<const uint16_t *>(base)[p] : base[p]);
+    if constexpr (WIDE) return 1u + reinterpret_cast<const uint16_t *>(base)[p];
+    else return 1u + base[p];
   }
   __device__ __forceinline__ void set(uint32_t p, uint32_t d) const {  // 0: none
-    if (wide)
+    if constexpr (WIDE)
       reinterpret_cast<uint16_t *>(base)[p] = static_cast<uint16_t>(d - 1);
     else
       base[p] = static_cast<uint8_t>(d - 1);
   }
 };
+
+// Little-endian 32-bit word of the chunk starting at byte b (any alignment;
+// reads the aligned words around it).
+__device__ __forceinline__ uint32_t bytes_at(const uint8_t *base, uint32_t b) {
+  const uint32_t *w = reinterpret_cast<const uint32_t *>(base + (b & ~3u));
+  const uint32_t sh = 8u * (b & 3u);
+  return sh ? __funnelshift_r(w[0], w[1], sh) : w[0];
+}
+
+// Key of position p: its first g symbols, S * g <= 8 little-endian bytes,
+// as two 32-bit words (the bytes beyond the key masked off).
+template <int S>
+__device__ __forceinline__ void key_at(const uint8_t *in, uint32_t p, uint32_t mlo,
+                                       uint32_t mhi, uint32_t &lo, uint32_t &hi) {
+  lo = bytes_at(in, p * S) & mlo;
+  hi = mhi ? bytes_at(in, p * S + 4) & mhi : 0u;
+}
 
 // Step 2: hash chains.  For every position p with room for m symbols, the
 // key is its first g = min(m, 8/S) symbols; the link of p is the distance to
@@ -75,11 +93,12 @@ struct Links {
 // the window.  A match of >= m symbols at p from offset d needs p - d to
 // carry the same key, so every such offset is on p's chain.
 // Bit p of `maybe` marks the positions whose chain can hold such an offset:
-// p has a link to q, and either q carries p's key or q's own chain goes on
-// within the window (a position with p's key behind q is on q's chain, at
-// most W back from p).  Unmarked positions have no offset with p's key in
-// the window, so skipping them as literals leaves the greedy parse
-// unchanged; the test drops most positions that only share a hash.
+// one of the first kFilterHops entries of p's chain within the window
+// carries p's key, or the chain goes on within the window beyond them.
+// Unmarked positions have no offset with p's key in the window, so skipping
+// them as literals leaves the greedy parse unchanged; the test drops the
+// positions that only share a hash (nearly all of them on data without
+// repeats, whose chunks then skip the parse altogether).
 //
 // The table holds the last position of each hash.  Slabs of 32 positions
 // go through it in order: each lane reads its bucket, then all lanes write
@@ -88,38 +107,39 @@ struct Links {
 // slabs need the lane groups of __match_any_sync (a shared unit with low
 // throughput).  The key filter runs after four slabs have been linked, on
 // independent loads.
-template <int S>
+constexpr uint32_t kFilterHops = 4;  // chain entries the candidate filter inspects
+
+template <int S, bool WIDE>
 __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
                                              uint32_t k, const BufDesc &A,
                                              const CompressSmem &sm, uint16_t *table,
-                                             uint32_t *maybe, const Links &links,
+                                             uint32_t *maybe, const Links<WIDE> &links,
                                              uint32_t lane) {
-  const uint32_t H = 1u << sm.hash_log2;
-  uint32_t *t32 = reinterpret_cast<uint32_t *>(table);
-  for (uint32_t i = lane; i < H / 2; i += 32) t32[i] = 0xFFFFFFFFu;
+  const uint32_t H = 1u << sm.hash_log2;  // >= 16
+  uint4 *t4 = reinterpret_cast<uint4 *>(table);
+  for (uint32_t i = lane; i < H / 8; i += 32) t4[i] = make_uint4(kFull, kFull, kFull, kFull);
   __syncwarp();
 
-  const uint32_t g = min(A.m, 8u / S);
-  const uint32_t tshift = 64u - sm.hash_log2;
+  const uint8_t *in = reinterpret_cast<const uint8_t *>(sym);
+  const uint32_t kb = S * min(A.m, 8u / S);  // key bytes
+  const uint32_t mlo = kb >= 4 ? kFull : (1u << (8 * kb)) - 1u;
+  const uint32_t mhi = kb <= 4 ? 0u : (kb >= 8 ? kFull : (1u << (8 * (kb - 4))) - 1u);
+  const uint32_t tshift = 32u - sm.hash_log2;
   const uint32_t lt = lanemask_lt(lane);
   const uint32_t nslab = (k + 31) / 32;
   constexpr uint32_t kGroup = 4;  // slabs whose hashes and filters are formed together
   for (uint32_t s0 = 0; s0 < nslab; s0 += kGroup) {
-    uint32_t hh[kGroup], qq[kGroup], dd[kGroup];
-    uint64_t kk[kGroup];
+    uint32_t hh[kGroup], klo[kGroup], khi[kGroup], qq[kGroup], dd[kGroup];
     bool okk[kGroup];
 #pragma unroll
     for (uint32_t u = 0; u < kGroup; ++u) {
       const uint32_t p = (s0 + u) * 32 + lane;
       const bool ok = s0 + u < nslab && p + A.m <= k;  // room for m symbols
-      uint64_t key = 0;
-      if (ok) {
-#pragma unroll
-        for (uint32_t i = 0; i < 8u / S; ++i)
-          if (i < g) key |= static_cast<uint64_t>(sym[p + i]) << (8 * S * i);
-      }
-      hh[u] = static_cast<uint32_t>((key * 0x9E3779B97F4A7C15ull) >> tshift);
-      kk[u] = key;
+      uint32_t lo = 0, hi = 0;
+      if (ok) key_at<S>(in, p, mlo, mhi, lo, hi);
+      hh[u] = ((hi * 0x85EBCA77u ^ lo) * 0x9E3779B1u) >> tshift;
+      klo[u] = lo;
+      khi[u] = hi;
       okk[u] = ok;
     }
     // links, slab after slab
@@ -151,23 +171,28 @@ __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
       dd[u] = dist;
     }
     __syncwarp();
-    // candidate filter: q's key, else whether q's chain goes on in reach
+    // candidate filter: walk p's chain for a position with p's key while it
+    // stays in the window (a few hops; past them p stays marked)
 #pragma unroll
     for (uint32_t u = 0; u < kGroup; ++u) {
-      const uint32_t base = (s0 + u) * 32;
-      const uint32_t q = qq[u], dist = dd[u];
-      const uint32_t dq_slab = __shfl_sync(kFull, dist, (q - base) & 31u);
+      uint32_t cur = qq[u], reach = dd[u];
       bool mb = false;
-      if (dist) {
-        uint64_t kq = 0;
-#pragma unroll
-        for (uint32_t i = 0; i < 8u / S; ++i)
-          if (i < g) kq |= static_cast<uint64_t>(sym[q + i]) << (8 * S * i);
-        if (kq == kk[u]) {
-          mb = true;
-        } else {
-          const uint32_t dq = q >= base ? dq_slab : links.get(q);
-          mb = dq != 0 && dist + dq <= A.W;
+      if (reach) {
+        for (uint32_t hop = 0;; ++hop) {
+          uint32_t lo, hi;
+          key_at<S>(in, cur, mlo, mhi, lo, hi);
+          if (lo == klo[u] && hi == khi[u]) {
+            mb = true;
+            break;
+          }
+          const uint32_t step = links.get(cur);  // >= 256 when none (see Links)
+          if (reach + step > A.W) break;
+          if (hop + 1 == kFilterHops) {
+            mb = true;
+            break;
+          }
+          cur -= step;
+          reach += step;
         }
       }
       const uint32_t mbits = __ballot_sync(kFull, mb);
@@ -189,14 +214,6 @@ __device__ __forceinline__ uint32_t extend(const typename SymType<S>::T *sym,
   uint32_t l = 0;
   while (l < cap && sym[p + l] == sym[p - d + l]) ++l;
   return l;
-}
-
-// Little-endian 32-bit word of the chunk starting at byte b (any alignment;
-// reads the aligned words around it).
-__device__ __forceinline__ uint32_t bytes_at(const uint8_t *base, uint32_t b) {
-  const uint32_t *w = reinterpret_cast<const uint32_t *>(base + (b & ~3u));
-  const uint32_t sh = 8u * (b & 3u);
-  return sh ? __funnelshift_r(w[0], w[1], sh) : w[0];
 }
 
 // extend() four bytes at a time: compare 32-bit words of the look-ahead and
@@ -225,10 +242,10 @@ constexpr uint32_t kChainWork = 384;
 // offset first, extending every offset d >= m that could still beat the
 // best; a strictly longer match replaces the best, so ties keep the nearest.
 // Returns false when the work cap stopped the walk with candidates left.
-template <int S>
+template <int S, bool WIDE>
 __device__ __forceinline__ bool chain_match(const typename SymType<S>::T *sym,
                                             uint32_t k, const BufDesc &A,
-                                            const Links &links, uint32_t q,
+                                            const Links<WIDE> &links, uint32_t q,
                                             uint32_t &best, uint32_t &bd) {
   const uint32_t lim = min(A.M, k - q);
   best = 0;
@@ -355,11 +372,11 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x, uint32_t lane,
 // chase marks the visited lanes; two warp scans give every visited lane its
 // token index and payload offset, and the lanes write their tokens and
 // literal runs in parallel.
-template <int S, int NJ>
+template <int S, int NJ, bool WIDE>
 __device__ __forceinline__ void greedy_walk(const typename SymType<S>::T *sym,
                                             uint32_t k, const BufDesc &A,
                                             const CompressSmem &sm, const uint32_t *maybe,
-                                            const Links &links, uint8_t *flags,
+                                            const Links<WIDE> &links, uint8_t *flags,
                                             uint8_t *pay, uint32_t lane,
                                             uint32_t &ntok_out, uint32_t &pay_out,
                                             bool &sane) {
@@ -406,7 +423,7 @@ __device__ __forceinline__ void greedy_walk(const typename SymType<S>::T *sym,
     const bool valid = lane < nvalid;
     uint32_t L = 0, bd = 0;
     bool resolved = true;
-    if (valid) resolved = chain_match<S>(sym, k, A, links, mypos, L, bd);
+    if (valid) resolved = chain_match<S, WIDE>(sym, k, A, links, mypos, L, bd);
     const uint32_t unres = __ballot_sync(kFull, !resolved);
     uint32_t nxt = valid ? mypos + (L >= A.m ? L : 1u) : k;
     uint32_t succ = count_below(mypos, nxt);
@@ -684,13 +701,13 @@ __device__ __forceinline__ void write_header(const BufDesc &B, uint32_t lane) {
 // Steps 1-5 for chunk c of buffer B (item `item` of a batch).  Returns false
 // when the TMA copy never landed (the warp must stop: its barrier phase is
 // unknown; the chunk was still published so no other warp waits on it).
-template <int S, int NJ>
+template <int S, int NJ, bool WIDE>
 __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufDesc &B,
                                                uint32_t item, uint32_t c, WarpState &W,
                                                uint32_t lane) {
   using Sym = typename SymType<S>::T;
   const Sym *sym = reinterpret_cast<const Sym *>(W.inb);
-  const Links links{W.links_base, B.W > 256};
+  const Links<WIDE> links{W.links_base};
   unsigned long long *status = A.status + B.gbase;
   if (c == 0) write_header(B, lane);
 
@@ -720,15 +737,26 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
   __syncwarp();
 
   // 2. candidate filter (hash table lives in the payload staging area)
-  build_chains<S>(sym, k, B, A.sm, reinterpret_cast<uint16_t *>(W.pay), W.maybe, links, lane);
+  build_chains<S, WIDE>(sym, k, B, A.sm, reinterpret_cast<uint16_t *>(W.pay), W.maybe, links,
+                        lane);
   const uint32_t fwords = (k + 31) / 32;
-  for (uint32_t i = lane; i < fwords; i += 32) reinterpret_cast<uint32_t *>(W.flags)[i] = 0;
+  uint32_t marked = 0;
+  for (uint32_t i = lane; i < fwords; i += 32) {
+    reinterpret_cast<uint32_t *>(W.flags)[i] = 0;
+    marked |= W.maybe[i];
+  }
   __syncwarp();
 
-  // 3. greedy parse + local offsets
-  uint32_t ntok, pb;
-  bool sane;
-  greedy_walk<S, NJ>(sym, k, B, A.sm, W.maybe, links, W.flags, W.pay, lane, ntok, pb, sane);
+  // 3. greedy parse + local offsets.  With no marked position the parse is
+  // k literals and the payload is the staged chunk itself.
+  uint32_t ntok = k, pb = k * S;
+  bool sane = true;
+  const uint8_t *payload = W.inb;
+  if (__any_sync(kFull, marked != 0)) {
+    greedy_walk<S, NJ, WIDE>(sym, k, B, A.sm, W.maybe, links, W.flags, W.pay, lane, ntok, pb,
+                             sane);
+    payload = W.pay;
+  }
   if (!sane && lane == 0) atomicOr(A.err, kErrInternal);
   const uint32_t fb = (ntok + 7) / 8;
   const uint64_t rec = static_cast<uint64_t>(fb) + pb;
@@ -746,7 +774,7 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
   drain_parked(A, W, false, lane);
   uint64_t excl;
   if (lookback_try(status, c, lane, excl)) {
-    place_record(A, B, c, excl, rec, W.flags, fb, W.pay, pb, data_ok, lane);
+    place_record(A, B, c, excl, rec, W.flags, fb, payload, pb, data_ok, lane);
   } else {
     const uint32_t free_mask =
         __ballot_sync(kFull, lane < A.park_slots && W.slot_c == kFreeSlot);
@@ -754,7 +782,7 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
       const uint32_t sidx = __ffs(free_mask) - 1;
       uint8_t *slot = W.slots + static_cast<uint64_t>(sidx) * A.park_slot_bytes;
       warp_copy(slot, W.flags, fb, lane);
-      warp_copy(slot + fb, W.pay, pb, lane);
+      warp_copy(slot + fb, payload, pb, lane);
       if (lane == sidx) {
         W.slot_c = c;
         W.slot_item = item;
@@ -762,7 +790,7 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
       }
     } else {
       const bool ok = lookback_wait(status, c, lane, A.err, excl);
-      place_record(A, B, c, excl, rec, W.flags, fb, W.pay, pb, data_ok && ok, lane);
+      place_record(A, B, c, excl, rec, W.flags, fb, payload, pb, data_ok && ok, lane);
     }
   }
   __syncwarp();
@@ -785,7 +813,8 @@ __global__ void __launch_bounds__(256) compress_kernel(const CompressArgs A) {
   while (true) {
     const uint32_t c = take_ticket(A.ticket, lane);
     if (c >= A.buf.nc) break;
-    if (!compress_chunk<S, NJ>(A, A.buf, 0, c, W, lane)) break;
+    // one-byte links exactly when W <= 256, which is when NJ <= 8
+    if (!compress_chunk<S, NJ, (NJ > 8)>(A, A.buf, 0, c, W, lane)) break;
   }
   drain_parked(A, W, true, lane);
 }
@@ -822,10 +851,26 @@ __global__ void __launch_bounds__(256) compress_batch_kernel(const CompressArgs 
     const BufDesc B = A.items[item];
     const uint32_t c = static_cast<uint32_t>(g - B.gbase);
     bool ok;
-    switch (B.S) {
-      case 1: ok = compress_chunk<1, NJ>(A, B, item, c, W, lane); break;
-      case 2: ok = compress_chunk<2, NJ>(A, B, item, c, W, lane); break;
-      default: ok = compress_chunk<4, NJ>(A, B, item, c, W, lane); break;
+    if constexpr (NJ > 8) {
+      if (B.W > 256) {
+        switch (B.S) {
+          case 1: ok = compress_chunk<1, NJ, true>(A, B, item, c, W, lane); break;
+          case 2: ok = compress_chunk<2, NJ, true>(A, B, item, c, W, lane); break;
+          default: ok = compress_chunk<4, NJ, true>(A, B, item, c, W, lane); break;
+        }
+      } else {
+        switch (B.S) {
+          case 1: ok = compress_chunk<1, NJ, false>(A, B, item, c, W, lane); break;
+          case 2: ok = compress_chunk<2, NJ, false>(A, B, item, c, W, lane); break;
+          default: ok = compress_chunk<4, NJ, false>(A, B, item, c, W, lane); break;
+        }
+      }
+    } else {
+      switch (B.S) {
+        case 1: ok = compress_chunk<1, NJ, false>(A, B, item, c, W, lane); break;
+        case 2: ok = compress_chunk<2, NJ, false>(A, B, item, c, W, lane); break;
+        default: ok = compress_chunk<4, NJ, false>(A, B, item, c, W, lane); break;
+      }
     }
     if (!ok) break;
   }
