@@ -15,6 +15,14 @@ are sampled with nvidia-smi during the timed region.  Under torchrun each
 rank compresses its own shard (independent data, weak scaling); there is no
 data-path collective.
 
+After the timed steps (not part of them) the line gets two more sections
+on the same GPU: `batched` -- 10,000 uneven buffers (4 KiB-16 MiB, four
+kinds, about 20 GB) compressed and decompressed by one persistent launch
+under a CUDA graph vs one plain launch per buffer -- and `served` -- a
+Poisson request stream (2000 requests/s, 10 s by default, --served 60 for
+the full trace) under continuous batching vs one launch per request, with
+p50/p99 latency.
+
 `--impl reference` times the CPU oracle (the plain definition) on a bounded
 sample of the same workload on the host cores.
 """
@@ -114,6 +122,36 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# The compression kernel's sources: a DRAM traffic figure from an ncu capture
+# holds only while these are unchanged.
+KERNEL_SOURCES = ("compress_impl.cuh", "compress_launch.cuh", "compress_s4.cu",
+                  "glz_common.h", "glz_device.cuh")
+PROFILE = os.path.join(ROOT, "profiles", "compress_kernel_field-256MiB.md")
+
+
+def kernel_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2304_07342_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of compress_kernel on the float field, from the
+    committed ncu summary, if it was taken on the current kernel sources."""
+    try:
+        fields = dict(line.strip().strip("- `").split(": ", 1) for line in open(PROFILE)
+                      if line.startswith("- `") and ": " in line)
+        sha = fields.get("sources_sha256", "").strip("` ")
+        if sha != kernel_sources_sha():
+            return None, "kernel changed since the ncu capture"
+        return int(fields["dram_bytes_per_launch"].strip("` ")), "ncu capture " + os.path.basename(PROFILE)
+    except (OSError, KeyError, ValueError):
+        return None, "no ncu capture"
 
 
 def _peaks():
@@ -244,6 +282,9 @@ def run_gpu(args):
     it0 = items[0]
     k_bytes = it0["d_in"].numel() + it0["size"]  # read input + write stream
     achieved = k_bytes / (k_ms * 1e-3) / 1e9
+    traffic, traffic_note = _profiled_traffic()
+    if args.workload not in ("field+indices", "field-256MiB"):
+        traffic, traffic_note = None, "ncu capture is of the float field workload"
     line = {
         "metric": METRIC,
         "value": round(n_in * world / (comp_ms * 1e-3) / 1e9, 3),
@@ -271,7 +312,9 @@ def run_gpu(args):
         "roofline": {"kernel": "compress_kernel (" + it0["label"] + ")",
                      "bound": "hbm", "achieved": round(achieved, 2),
                      "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 5),
-                     "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+                     "traffic": traffic, "traffic_source": traffic_note,
+                     "algorithmic_bytes": k_bytes,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
         "e2e": e2e,
         "gpu_launches": args.steps * len(items) * 2,
         "clocks": clk.summary(),
