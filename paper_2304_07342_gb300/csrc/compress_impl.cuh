@@ -202,6 +202,104 @@ __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
   }
 }
 
+// Literal pre-check: true only when no position of the chunk can start a
+// match of >= m symbols, so that the greedy parse is k literals (section
+// 2.2: a position without a match is emitted as a literal) and the chains
+// need not be built.  It is exact in both directions that matter: it never
+// returns true for a chunk with a match, and on data without repeats it
+// returns true after one shared-memory atomic per position.
+//
+// Every position with room for m symbols ORs a 3-bit mask, drawn from a hash
+// of its key (its first g symbols, as for the chains), into one 32-bit word
+// of a bitmap that starts empty (a blocked Bloom filter over the keys seen
+// so far in the chunk).  The atomic returns the word before the OR; a
+// position finds all its bits already set ("flagged") whenever an earlier
+// position of an earlier slab has its key.  Two positions of one slab that
+// share a key are ordered by the atomic unit, not by position, so it is the
+// one processed second that is flagged, which may be the earlier position.
+// So a flagged position p is checked exactly, by the whole warp, for
+//   (i)  a match of >= m symbols at p from an offset d in [m, min(W, p)], and
+//   (ii) a match of >= m symbols at a later position of p's own slab from p;
+// and any hit (or more than kBloomMaxFlagged flagged positions) sends the
+// chunk to the full path.  If some position q has a match from p = q - d,
+// then p and q share the key: q is flagged (and (i) finds it) unless p and q
+// lie in one slab and p came second, in which case p is flagged and (ii)
+// finds it.
+constexpr uint32_t kBloomMaxFlagged = 16;
+
+// Does p (flagged, p + m <= k) take part in a match of >= m symbols, as the
+// position coded ((i)) or as the source of a later position of its slab
+// that ends at `slab_end` ((ii))?  Warp-wide; every lane returns the answer.
+template <int S>
+__device__ __forceinline__ bool match_near(const typename SymType<S>::T *sym, uint32_t k,
+                                           const BufDesc &A, uint32_t p, uint32_t slab_end,
+                                           uint32_t lane) {
+  const uint32_t dmax = min(A.W, p);
+  bool hit = false;
+  for (uint32_t d0 = 0; d0 < dmax; d0 += 32) {
+    const uint32_t d = d0 + lane + 1;
+    bool eq = d >= A.m && d <= dmax;
+    for (uint32_t i = 0; eq && i < A.m; ++i) eq = sym[p + i] == sym[p - d + i];
+    hit |= eq;
+  }
+  const uint32_t q = p + 1 + lane;
+  bool eq = q < slab_end && q - p >= A.m && q - p <= A.W && q + A.m <= k;
+  for (uint32_t i = 0; eq && i < A.m; ++i) eq = sym[q + i] == sym[p + i];
+  hit |= eq;
+  return __any_sync(kFull, hit);
+}
+
+template <int S>
+__device__ __forceinline__ bool literal_chunk(const typename SymType<S>::T *sym, uint32_t k,
+                                              const BufDesc &A, uint32_t *bm, uint32_t bl,
+                                              uint32_t *maybe, uint32_t lane) {
+  uint4 *b4 = reinterpret_cast<uint4 *>(bm);
+  for (uint32_t i = lane; i < (1u << bl) / 4; i += 32) b4[i] = make_uint4(0, 0, 0, 0);
+  __syncwarp();
+  const uint8_t *in = reinterpret_cast<const uint8_t *>(sym);
+  const uint32_t kb = S * min(A.m, 8u / S);  // key bytes, as in build_chains
+  const uint32_t mlo = kb >= 4 ? kFull : (1u << (8 * kb)) - 1u;
+  const uint32_t mhi = kb <= 4 ? 0u : (kb >= 8 ? kFull : (1u << (8 * (kb - 4))) - 1u);
+  const uint32_t wshift = 32u - bl;
+  const uint32_t nslab = (k + 31) / 32;
+  uint32_t nflag = 0;
+  for (uint32_t s = 0; s < nslab; ++s) {
+    const uint32_t p = s * 32 + lane;
+    const bool ok = p + A.m <= k;
+    uint32_t lo = 0, hi = 0;
+    if (ok) key_at<S>(in, p, mlo, mhi, lo, hi);
+    const uint32_t h = ((hi * 0x85EBCA77u) ^ lo) * 0x9E3779B1u;
+    const uint32_t g = h * 0xC2B2AE3Du;
+    const uint32_t mask =
+        (1u << (g >> 27)) | (1u << ((g >> 22) & 31u)) | (1u << ((g >> 17) & 31u));
+    uint32_t old = 0;
+    if (ok) old = atomicOr(&bm[h >> wshift], mask);
+    const uint32_t f = __ballot_sync(kFull, ok && (old & mask) == mask);
+    if (lane == 0) maybe[s] = f;
+    nflag += __popc(f);
+    if (nflag > kBloomMaxFlagged) return false;
+    __syncwarp();  // this slab's ORs before the next slab's
+  }
+  __syncwarp();
+  if (nflag == 0) return true;
+  for (uint32_t w0 = 0; w0 < nslab; w0 += 32) {
+    const uint32_t f = w0 + lane < nslab ? maybe[w0 + lane] : 0u;
+    uint32_t has = __ballot_sync(kFull, f != 0);
+    while (has) {
+      const uint32_t j = __ffs(has) - 1;
+      has &= has - 1;
+      uint32_t bits = __shfl_sync(kFull, f, j);
+      const uint32_t s = w0 + j;
+      while (bits) {
+        const uint32_t p = s * 32 + __ffs(bits) - 1;
+        bits &= bits - 1;
+        if (match_near<S>(sym, k, A, p, min(k, s * 32 + 32), lane)) return false;
+      }
+    }
+  }
+  return true;
+}
+
 __device__ __forceinline__ void warp_copy_bytes(uint8_t *dst, const uint8_t *src,
                                                 uint32_t nbytes, uint32_t lane) {
   warp_copy(dst, src, nbytes, lane);
@@ -736,15 +834,22 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
   }
   __syncwarp();
 
-  // 2. candidate filter (hash table lives in the payload staging area)
-  build_chains<S, WIDE>(sym, k, B, A.sm, reinterpret_cast<uint16_t *>(W.pay), W.maybe, links,
-                        lane);
-  const uint32_t fwords = (k + 31) / 32;
+  // 2. literal pre-check (when the payload area holds a bitmap of >= 16
+  // bits per position), else the candidate filter (hash table in the
+  // payload staging area)
+  const uint32_t bl = 31u - __clz(A.sm.pay_bytes / 4);  // bitmap words = 2^bl
+  bool literal = false;
+  if (bl >= 2 && (2u << bl) >= k)
+    literal = literal_chunk<S>(sym, k, B, reinterpret_cast<uint32_t *>(W.pay), bl, W.maybe,
+                               lane);
   uint32_t marked = 0;
-  for (uint32_t i = lane; i < fwords; i += 32) {
-    reinterpret_cast<uint32_t *>(W.flags)[i] = 0;
-    marked |= W.maybe[i];
+  if (!literal) {
+    build_chains<S, WIDE>(sym, k, B, A.sm, reinterpret_cast<uint16_t *>(W.pay), W.maybe,
+                          links, lane);
+    for (uint32_t i = lane; i < (k + 31) / 32; i += 32) marked |= W.maybe[i];
   }
+  for (uint32_t i = lane; i < (k + 31) / 32; i += 32)
+    reinterpret_cast<uint32_t *>(W.flags)[i] = 0;
   __syncwarp();
 
   // 3. greedy parse + local offsets.  With no marked position the parse is

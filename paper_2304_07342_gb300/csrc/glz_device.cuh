@@ -110,7 +110,9 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(
   return v;
 }
 
-// Warp copy of n bytes between any two addresses (shared or global): the
+// Warp copy of n bytes between any two addresses (shared or global).  When
+// source and destination share their alignment modulo 16 (and n >= 256) the
+// body moves as 16-byte words.  Otherwise the
 // destination is written in aligned 32-bit words, each assembled from two
 // aligned source words with a funnel shift; unaligned head and tail bytes
 // are copied singly.  Eight words per lane are loaded before any is stored,
@@ -121,6 +123,28 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(
 __device__ __forceinline__ void warp_copy(uint8_t *dst, const uint8_t *src,
                                           uint32_t n, uint32_t lane) {
   constexpr uint32_t U = 8;
+  if ((((reinterpret_cast<uintptr_t>(dst) ^ reinterpret_cast<uintptr_t>(src)) & 15u) == 0) &&
+      n >= 256) {
+    // co-aligned: 16-byte words, four per lane in flight
+    const uint32_t h16 =
+        (16u - static_cast<uint32_t>(reinterpret_cast<uintptr_t>(dst) & 15u)) & 15u;
+    if (lane < h16) dst[lane] = src[lane];
+    const uint32_t q = (n - h16) >> 4;
+    const uint4 *s16 = reinterpret_cast<const uint4 *>(src + h16);
+    uint4 *d16 = reinterpret_cast<uint4 *>(dst + h16);
+    uint32_t j = lane;
+    for (; j + 96 < q; j += 128) {
+      const uint4 a = s16[j], b = s16[j + 32], c = s16[j + 64], d = s16[j + 96];
+      d16[j] = a;
+      d16[j + 32] = b;
+      d16[j + 64] = c;
+      d16[j + 96] = d;
+    }
+    for (; j < q; j += 32) d16[j] = s16[j];
+    const uint32_t done16 = h16 + 16u * q;
+    if (lane < n - done16) dst[done16 + lane] = src[done16 + lane];
+    return;
+  }
   const uint32_t head =
       min(n, (4u - static_cast<uint32_t>(reinterpret_cast<uintptr_t>(dst) & 3u)) & 3u);
   if (lane < head) dst[lane] = src[lane];
