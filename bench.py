@@ -15,8 +15,10 @@ are sampled with nvidia-smi during the timed region.  Under torchrun each
 rank compresses its own shard (independent data, weak scaling); there is no
 data-path collective.
 
-After the timed steps (not part of them) the line gets two more sections
-on the same GPU: `batched` -- 10,000 uneven buffers (4 KiB-16 MiB, four
+After the timed steps (not part of them) the line gets three more sections
+on the same GPU: `paper_matcher` -- the paper's own matcher (section 3.3.2)
+beside the exact one on 256 MiB of uint16 quantization codes; `batched` --
+10,000 uneven buffers (4 KiB-16 MiB, four
 kinds, about 20 GB) compressed and decompressed by one persistent launch
 under a CUDA graph vs one plain launch per buffer -- and `served` -- a
 Poisson request stream (2000 requests/s, 10 s by default, --served 60 for
@@ -272,6 +274,7 @@ def run_gpu(args):
     # end to end through the public API with host buffers: pinned input ->
     # device, compress, compressed stream -> pinned host, every step
     e2e = _e2e(codec, items, stream, args)
+    v2 = _version2(codec, items, stream) if args.version2 else None
 
     if rank != 0:
         if world > 1:
@@ -317,6 +320,7 @@ def run_gpu(args):
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
         "e2e": e2e,
         "gpu_launches": args.steps * len(items) * 2,
+        "stream_version2": v2,
         "clocks": clk.summary(),
     }
     if args.cpu_baseline:
@@ -329,11 +333,44 @@ def run_gpu(args):
         for k in ("d_in", "d_out", "d_dec"):
             it[k] = None
     torch.cuda.empty_cache()
+    if args.paper_matcher:
+        line["paper_matcher"] = _paper_matcher(torch, codec, args)
     if args.batched:
         line["batched"] = _batched(torch, codec, args)
     if args.served > 0:
         line["served"] = _served(torch, codec, args, args.served)
     return line
+
+
+def _paper_matcher(torch, codec, args, n_sym: int = 128 << 20):
+    """The paper's own matcher (section 3.3.2) beside the exact one, on 256
+    MiB of uint16 quantization codes with the small workload's parameters
+    (S=2, C=4096, W=128, m=3, M=255): compression GB/s and ratio of each."""
+    from paper_2304_07342_gb300 import lz, synth
+    x = synth.quant_codes_laplace(n_sym, seed=args.seed)
+    d = torch.from_numpy(x.view(np.uint8)).cuda()
+    P = lz.Params(2, 4096, 128, 3, 255)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"uint16 quant codes, {d.numel() >> 20} MiB", "params": "S=2 C=4096 W=128 m=3 M=255"}
+    for name, mode in (("exact", lz.LZ_MATCH_EXACT), ("paper", lz.LZ_MATCH_PAPER)):
+        buf, nb = codec.compress(d, P, match=mode)
+        for _ in range(3):
+            codec.compress(d, P, out=buf, out_bytes=nb, match=mode)
+        if codec.sync() != lz.LZ_OK:
+            raise RuntimeError("compress failed on the device")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(5):
+            codec.compress(d, P, out=buf, out_bytes=nb, match=mode)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 5
+        out[name] = {"compress_gbs": round(d.numel() / (ms * 1e-3) / 1e9, 3),
+                     "ratio": round(d.numel() / int(nb.item()), 4)}
+        del buf
+    del d
+    torch.cuda.empty_cache()
+    return out
 
 
 def _batched(torch, codec, args, n_buffers: int = 10_000):
@@ -366,6 +403,56 @@ def _served(torch, codec, args, seconds: float, budget: int = 40 * 10 ** 9):
     return {"workload": f"2000 req/s Poisson for {seconds:g} s, 70% compress, "
                         "lognormal(256 KiB, 1.5) sizes capped at 64 MiB, S in {1,2,4}",
             "budget_bytes": budget, "batched": b, "plain": p}
+
+
+def _version2(codec, items, stream, reps: int = 5):
+    """The same items compressed as stream version 2 (a chunk that would not
+    shrink is stored as it is) and decompressed again: GB/s and ratio,
+    CUDA events over `reps` passes (after one checked pass)."""
+    import torch
+
+    from paper_2304_07342_gb300 import lz
+    for it in items:
+        lz.lz_compress_ex(codec.ctx, it["d_in"].data_ptr(), it["d_in"].numel(), it["p"],
+                          it["d_out"].data_ptr(), it["cap"], it["d_nb"].data_ptr(),
+                          stream.cuda_stream, version=2)
+    if codec.sync() != lz.LZ_OK:
+        raise RuntimeError("version-2 compress failed on the device")
+    sizes = [int(it["d_nb"].item()) for it in items]
+    for it, sz in zip(items, sizes):
+        lz.lz_decompress(codec.ctx, it["d_out"].data_ptr(), sz, it["d_dec"].data_ptr(),
+                         it["d_dec"].numel(), it["d_db"].data_ptr(), stream.cuda_stream)
+    if codec.sync() != lz.LZ_OK:
+        raise RuntimeError("version-2 decompress failed on the device")
+    for it in items:
+        if not torch.equal(it["d_dec"], it["d_in"]):
+            raise RuntimeError(f"version-2 round trip mismatch: {it['label']}")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    for _ in range(reps):
+        for it in items:
+            lz.lz_compress_ex(codec.ctx, it["d_in"].data_ptr(), it["d_in"].numel(), it["p"],
+                              it["d_out"].data_ptr(), it["cap"], it["d_nb"].data_ptr(),
+                              stream.cuda_stream, version=2)
+    ev[1].record(stream)
+    for _ in range(reps):
+        for it, sz in zip(items, sizes):
+            lz.lz_decompress(codec.ctx, it["d_out"].data_ptr(), sz, it["d_dec"].data_ptr(),
+                             it["d_dec"].numel(), it["d_db"].data_ptr(), stream.cuda_stream)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    n_in = sum(it["d_in"].numel() for it in items)
+    c_ms = ev[0].elapsed_time(ev[1]) / reps
+    d_ms = ev[1].elapsed_time(ev[2]) / reps
+    # restore the version-1 streams the rest of the run expects
+    for it in items:
+        lz.lz_compress(codec.ctx, it["d_in"].data_ptr(), it["d_in"].numel(), it["p"],
+                       it["d_out"].data_ptr(), it["cap"], it["d_nb"].data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    return {"compress_gbs": round(n_in / (c_ms * 1e-3) / 1e9, 3),
+            "decompress_gbs": round(n_in / (d_ms * 1e-3) / 1e9, 3),
+            "ratio": round(n_in / sum(sizes), 5),
+            "note": "same items, lz_compress_ex version 2 (stored chunks); not the headline"}
 
 
 def _e2e(codec, items, stream, args):
@@ -457,6 +544,10 @@ def main():
     ap.add_argument("--workload", default="field+indices")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-version2", dest="version2", action="store_false",
+                    help="skip the stream-version-2 (stored chunks) pass")
+    ap.add_argument("--no-paper-matcher", dest="paper_matcher", action="store_false",
+                    help="skip the exact-vs-paper matcher comparison")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 10,000-buffer batched comparison")
     ap.add_argument("--served", type=float, default=10.0,

@@ -60,6 +60,18 @@ typedef struct lz_params {
   uint32_t max_match;    /* M: min_match..255 (one length byte, 3.3.2)   */
 } lz_params;
 
+/* Matcher of the greedy parse.  Both give streams of the same layout,
+ * decoded by lz_decompress. */
+typedef enum lz_match {
+  LZ_MATCH_EXACT = 0, /* longest match, nearest offset on ties (section 2.2
+                         step 2, the definition; what lz_compress uses)   */
+  LZ_MATCH_PAPER = 1  /* the paper's own matcher (section 3.3.2, the four
+                         steps of its matching method): a forward scan of
+                         the window from its far end whose search pointer
+                         never moves back, keeping the first run of the
+                         greatest length; it can miss the longest match */
+} lz_match;
+
 typedef enum lz_status {
   LZ_OK = 0,
   LZ_ERR_INVALID_ARG = 1,      /* bad pointer, size or parameter          */
@@ -108,6 +120,28 @@ uint64_t lz_compressed_bound(uint64_t n_bytes, const lz_params *p);
 lz_status lz_compress(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
                       const lz_params *p, void *d_out, uint64_t out_cap,
                       uint64_t *d_out_bytes, lz_stream_t stream);
+
+/* Options of lz_compress_ex.  A zero-initialised struct means
+ * LZ_MATCH_EXACT and stream version 1, i.e. exactly lz_compress. */
+typedef struct lz_options {
+  uint32_t match;   /* lz_match                                          */
+  uint32_t version; /* stream version written: 0 or 1 = GLZ1 version 1   */
+} lz_options;
+
+/* lz_compress with options (opt may be NULL: the defaults).
+ * opt->match = LZ_MATCH_PAPER parses with the paper's matcher (section
+ * 3.3.2): at coding position p the scan runs from max(0, p - W); a run
+ * that ends at a mismatch is kept if strictly longer than the best so far,
+ * and the scan resumes at the symbol after the one that broke it; the scan
+ * ends when a run reaches p or the end of the look-ahead, min(k, p + M)
+ * symbols; the parse takes a pointer when the kept run has >= m symbols.
+ * Positions without any match of >= m symbols are literals under both
+ * matchers, and the stream header does not record the matcher.
+ * LZ_ERR_INVALID_ARG for an unknown matcher or version; everything else as
+ * for lz_compress. */
+lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
+                         const lz_params *p, const lz_options *opt, void *d_out,
+                         uint64_t out_cap, uint64_t *d_out_bytes, lz_stream_t stream);
 
 /* Read and validate the header of the stream at d_in (in_bytes long) and
  * return its decompressed size in *h_n.  Synchronises `stream` (it copies
@@ -189,14 +223,34 @@ void lz_batch_destroy(lz_batch *batch, lz_stream_t stream);
 
 /* Choose chunk_bytes and window for data of `symbol_bytes`-byte symbols from
  * timed trial compressions of a device-resident sample: among C in {2048,
- * 4096, 8192} and W in {64, 128, 256}, the fastest whose compression ratio
- * is within 2% of the best ratio found; min_match 3 (2 for 4-byte symbols),
+ * 4096, 8192} and W in {64, 128, 256} whose compression ratio is within 2%
+ * of the best ratio found, the smallest C that is within 10% of the fastest
+ * time (less shared memory per warp, which helps a batched launch over
+ * buffers of several kinds), then the fastest; min_match 3 (2 for 4-byte symbols),
  * max_match 255.  The choice changes the stream (it is recorded in its
  * header), never the arithmetic: the stream is exactly what lz_compress
  * produces with the chosen parameters.  Synchronous; allocates and frees
  * temporary device buffers. */
 lz_status lz_autotune(lz_ctx *ctx, const void *d_sample, uint64_t sample_bytes,
                       uint32_t symbol_bytes, lz_params *out);
+
+/* The paper's parameter selection (section 3.2.3), for data whose elements
+ * are dtype_bytes wide (1, 2 or 4) at compression level `level` (1-4,
+ * windows 32/64/128/255 symbols; a higher level gives a better ratio at a
+ * lower throughput).  Multi-byte matching is the default: S = dtype_bytes
+ * and the level's window enlarged S times (at most 1024).  The sample at
+ * d_sample (device, sample_bytes rounded down to a multiple of
+ * dtype_bytes) is compressed with it; when its compression ratio
+ * (sample bytes / stream bytes) is below 1.5 the policy falls back to
+ * single-byte matching, S = 1 with the level's window.  In both cases
+ * C = chunk_bytes, M = 255 and m = the shortest profitable match,
+ * (1 + offB) / S + 1 (integer division).  dtype_bytes = 1 needs no trial.
+ * Writes the chosen parameters to *out.  Synchronises `stream`; allocates
+ * and frees temporary device buffers (stream-ordered).  LZ_ERR_INVALID_ARG
+ * for a bad dtype, level or chunk size or an empty sample. */
+lz_status lz_select_params(lz_ctx *ctx, const void *d_sample, uint64_t sample_bytes,
+                           uint32_t dtype_bytes, uint32_t level, uint32_t chunk_bytes,
+                           lz_params *out, lz_stream_t stream);
 
 /* Stitch one shard stream into a whole-input stream.  Chunks are
  * independent (section 3.3.1), so the stream of bytes [b0, b1) of an input

@@ -12,7 +12,10 @@ computes, and which passage of the paper it follows, is documented in
 
 * :func:`longest_match` -- section 2.2 step 2 over S-byte symbols (3.2.3),
   nearest offset on ties, length <= offset (3.3.2);
-* :func:`parse_chunk` -- section 2.2 steps 1-6 inside one chunk (3.3.1);
+* :func:`paper_match` -- the paper's own matcher (section 3.3.2, its four
+  matching steps), a heuristic that never exceeds :func:`longest_match`;
+* :func:`parse_chunk` -- section 2.2 steps 1-6 inside one chunk (3.3.1),
+  with either matcher;
 * :func:`compress` / :func:`decompress` -- the whole chunked stream.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
@@ -73,6 +76,18 @@ def _load():
         lib.lzref_parse_chunk.argtypes = [u8p, u32, u32, u32, u32, u32,
                                           u32p, u32p]
         lib.lzref_parse_chunk.restype = u32
+        lib.lzref_paper_match.argtypes = [u8p, u32, u32, u32, u32, u32,
+                                          u32p, u32p]
+        lib.lzref_paper_match.restype = None
+        lib.lzref_parse_chunk_mode.argtypes = [u8p, u32, u32, u32, u32, u32,
+                                               u32, u32p, u32p]
+        lib.lzref_parse_chunk_mode.restype = u32
+        lib.lzref_compress_mode.argtypes = [u8p, u64] + [u32] * 6 + [
+            u8p, u64, u64p]
+        lib.lzref_compress_mode.restype = ctypes.c_int
+        lib.lzref_compress_v.argtypes = [u8p, u64] + [u32] * 7 + [
+            u8p, u64, u64p]
+        lib.lzref_compress_v.restype = ctypes.c_int
         lib.lzref_compress.argtypes = [u8p, u64] + [u32] * 5 + [u8p, u64,
                                                                 u64p]
         lib.lzref_compress.restype = ctypes.c_int
@@ -124,29 +139,49 @@ def longest_match(chunk, p_sym: int, S: int, W: int, M: int = 255):
     return ln.value, off.value
 
 
-def parse_chunk(chunk, S: int, W: int, m: int, M: int = 255):
-    """Greedy tokens of one chunk as a list of (len, off); off 0 = literal."""
+def paper_match(chunk, p_sym: int, S: int, W: int, M: int = 255):
+    """(len, off) found at symbol ``p_sym`` by the paper's matcher (section
+    3.3.2: forward scan, search pointer never moved back, first run of the
+    greatest length)."""
+    b = _bytes(chunk)
+    k = b.size // S
+    ln, off = ctypes.c_uint32(), ctypes.c_uint32()
+    _load().lzref_paper_match(_ptr(b), k, p_sym, S, W, M,
+                              ctypes.byref(ln), ctypes.byref(off))
+    return ln.value, off.value
+
+
+MATCH_EXACT, MATCH_PAPER = 0, 1
+
+
+def parse_chunk(chunk, S: int, W: int, m: int, M: int = 255,
+                mode: int = MATCH_EXACT):
+    """Greedy tokens of one chunk as a list of (len, off); off 0 = literal.
+    ``mode`` picks the matcher: MATCH_EXACT (longest, nearest) or
+    MATCH_PAPER (the paper's scan)."""
     b = _bytes(chunk)
     k = b.size // S
     tl = np.zeros(max(k, 1), np.uint32)
     to = np.zeros(max(k, 1), np.uint32)
-    nt = _load().lzref_parse_chunk(
-        _ptr(b), k, S, W, m, M,
+    nt = _load().lzref_parse_chunk_mode(
+        _ptr(b), k, S, W, m, M, mode,
         tl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
         to.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
     return [(int(tl[i]), int(to[i])) for i in range(nt)]
 
 
-def compress(data, p: Params) -> np.ndarray:
-    """Compressed GLZ1 stream of ``data`` (any numpy array, taken as bytes)."""
+def compress(data, p: Params, mode: int = MATCH_EXACT, version: int = 1) -> np.ndarray:
+    """Compressed GLZ1 stream of ``data`` (any numpy array, taken as bytes),
+    parsed with the matcher ``mode``, in stream version ``version`` (2 adds
+    stored chunks, see lzref.h)."""
     b = _bytes(data)
     cap = bound(b.size, p)
     if cap == 0:
         raise OracleError(EINVAL, "bound")
     out = np.empty(cap, np.uint8)
     nb = ctypes.c_uint64()
-    rc = _load().lzref_compress(_ptr(b), b.size, *p.tuple(), _ptr(out), cap,
-                                ctypes.byref(nb))
+    rc = _load().lzref_compress_v(_ptr(b), b.size, *p.tuple(), mode, version,
+                                  _ptr(out), cap, ctypes.byref(nb))
     if rc != OK:
         raise OracleError(rc, "compress")
     return out[: nb.value].copy()
@@ -184,3 +219,44 @@ def decompress_status(stream) -> int:
     nb = ctypes.c_uint64()
     return _load().lzref_decompress(_ptr(b), b.size, _ptr(out), n.value,
                                     ctypes.byref(nb))
+
+
+# --- parameter policy (section 3.2.3) -----------------------------------------
+
+LEVEL_WINDOWS = (32, 64, 128, 255)  # levels 1-4: window in symbols
+
+
+def min_profitable_match(S: int, W: int) -> int:
+    """Smallest match length whose pointer (one length byte plus a one- or
+    two-byte offset) is shorter than the S-byte literals it replaces."""
+    offB = 1 if W <= 256 else 2
+    return (1 + offB) // S + 1
+
+
+def ratio_below(n_bytes: int, stream_bytes: int, num: int = 3, den: int = 2) -> bool:
+    """n / stream < num / den, in integers (the ratio test of the policy)."""
+    return n_bytes * den < num * stream_bytes
+
+
+def select_params(sample, dtype_bytes: int, level: int = 3,
+                  chunk_bytes: int = 4096) -> Params:
+    """The paper's parameter selection (section 3.2.3).  The symbol length
+    starts at the data type's size (multi-byte matching, the default) with
+    the level's window enlarged S times; the sample is compressed with it,
+    and when its compression ratio is below 1.5 the policy falls back to
+    single-byte matching with the level's window.  The minimum match is the
+    shortest profitable one, the maximum 255."""
+    if dtype_bytes not in (1, 2, 4) or level not in (1, 2, 3, 4):
+        raise OracleError(EINVAL, "select_params")
+    Wl = LEVEL_WINDOWS[level - 1]
+    single = Params(1, chunk_bytes, Wl, min_profitable_match(1, Wl), 255)
+    if dtype_bytes == 1:
+        return single
+    Wm = min(1024, dtype_bytes * Wl)
+    multi = Params(dtype_bytes, chunk_bytes, Wm, min_profitable_match(dtype_bytes, Wm), 255)
+    b = _bytes(sample)
+    b = b[: b.size - b.size % dtype_bytes]
+    if b.size == 0:
+        raise OracleError(EINVAL, "select_params")
+    size = compress(b, multi).size
+    return single if ratio_below(b.size, size) else multi

@@ -92,14 +92,80 @@ void lzref_longest_match(const uint8_t *chunk, uint32_t k, uint32_t p,
   *off = best_d;
 }
 
+/* The paper's own matcher (section 3.3.2, the four steps of its matching
+ * method), over S-byte symbols.  Two pointers: the search pointer starts
+ * at the beginning of the window, the position pointer at the coding
+ * position p.
+ *   - While the two point at equal symbols, both advance (a run); the
+ *     offset of the run is the distance between them when it started.
+ *   - At a mismatch the run ends: it is recorded if strictly longer than
+ *     the longest so far; the position pointer goes back to p and the
+ *     search pointer advances by one from where it stopped (it is never
+ *     moved back, which is why the method can miss the longest match).
+ *   - Before a run starts, a mismatch just advances the search pointer.
+ *   - The scan ends when the search pointer reaches p (so a match never
+ *     runs into the coding position: length <= offset) or the position
+ *     pointer reaches the end of the look-ahead.
+ * Readings where the printed loop is silent: the look-ahead ends at the
+ * chunk end or M symbols after p, whichever comes first (the length field
+ * is one byte); a run still in progress when the scan ends is compared
+ * like any other (otherwise a run that reaches p would never count).
+ * Ties keep the first run found, i.e. the farthest offset. */
+void lzref_paper_match(const uint8_t *chunk, uint32_t k, uint32_t p,
+                       uint32_t S, uint32_t W, uint32_t M, uint32_t *len,
+                       uint32_t *off) {
+  uint32_t search = p > W ? p - W : 0;
+  uint32_t ahead_end = (k - p < M) ? k : p + M;
+  uint32_t pos = p;
+  uint32_t run = 0, run_off = 0, best = 0, best_off = 0;
+  while (search < p && pos < ahead_end) {
+    if (ref_sym_eq(chunk, S, pos, search)) {
+      if (run == 0) run_off = pos - search;
+      ++run;
+      ++pos;
+    } else {
+      if (run > best) {
+        best = run;
+        best_off = run_off;
+      }
+      run = 0;
+      run_off = 0;
+      pos = p;
+    }
+    ++search;
+  }
+  if (run > best) {
+    best = run;
+    best_off = run_off;
+  }
+  *len = best;
+  *off = best_off;
+}
+
+typedef void (*ref_matcher)(const uint8_t *, uint32_t, uint32_t, uint32_t,
+                            uint32_t, uint32_t, uint32_t *, uint32_t *);
+
+static ref_matcher ref_matcher_of(uint32_t mode) {
+  return mode == LZREF_MATCH_PAPER ? lzref_paper_match : lzref_longest_match;
+}
+
 /* Section 2.2 steps 1, 3, 4, 6: greedy parse from the chunk start. */
 uint32_t lzref_parse_chunk(const uint8_t *chunk, uint32_t k, uint32_t S,
                            uint32_t W, uint32_t m, uint32_t M,
                            uint32_t *tok_len, uint32_t *tok_off) {
+  return lzref_parse_chunk_mode(chunk, k, S, W, m, M, LZREF_MATCH_EXACT,
+                                tok_len, tok_off);
+}
+
+uint32_t lzref_parse_chunk_mode(const uint8_t *chunk, uint32_t k, uint32_t S,
+                                uint32_t W, uint32_t m, uint32_t M,
+                                uint32_t mode, uint32_t *tok_len,
+                                uint32_t *tok_off) {
+  ref_matcher match = ref_matcher_of(mode);
   uint32_t p = 0, t = 0;
   while (p < k) {
     uint32_t len, off;
-    lzref_longest_match(chunk, k, p, S, W, M, &len, &off);
+    match(chunk, k, p, S, W, M, &len, &off);
     if (len >= m) {
       tok_len[t] = len;
       tok_off[t] = off;
@@ -134,7 +200,23 @@ static uint64_t ref_get_u64(const uint8_t *src) {
 int lzref_compress(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
                    uint32_t W, uint32_t m, uint32_t M, uint8_t *out,
                    uint64_t cap, uint64_t *out_bytes) {
+  return lzref_compress_mode(in, n, S, C, W, m, M, LZREF_MATCH_EXACT, out, cap,
+                             out_bytes);
+}
+
+int lzref_compress_mode(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
+                        uint32_t W, uint32_t m, uint32_t M, uint32_t mode,
+                        uint8_t *out, uint64_t cap, uint64_t *out_bytes) {
+  return lzref_compress_v(in, n, S, C, W, m, M, mode, 1, out, cap, out_bytes);
+}
+
+int lzref_compress_v(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
+                     uint32_t W, uint32_t m, uint32_t M, uint32_t mode,
+                     uint32_t version, uint8_t *out, uint64_t cap,
+                     uint64_t *out_bytes) {
   if (lzref_check_params(S, C, W, m, M) != REF_OK) return REF_EINVAL;
+  if (mode != LZREF_MATCH_EXACT && mode != LZREF_MATCH_PAPER) return REF_EINVAL;
+  if (version != 1 && version != 2) return REF_EINVAL;
   if (n % S != 0) return REF_EINVAL;
   uint64_t nc = ref_div_up(n, C);
   if (nc > 0xFFFFFFFFull) return REF_EINVAL;
@@ -147,7 +229,7 @@ int lzref_compress(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
 
   memset(out, 0, (size_t)records_at);
   memcpy(out, "GLZ1", 4);
-  out[4] = 1;
+  out[4] = (uint8_t)version;
   out[5] = (uint8_t)S;
   out[6] = (uint8_t)offB;
   out[7] = (uint8_t)m;
@@ -172,7 +254,8 @@ int lzref_compress(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
     const uint8_t *chunk = in + c * (uint64_t)C;
     uint64_t bytes = (c + 1 < nc) ? C : n - c * (uint64_t)C;
     uint32_t k = (uint32_t)(bytes / S);
-    uint32_t ntok = lzref_parse_chunk(chunk, k, S, W, m, M, tok_len, tok_off);
+    uint32_t ntok =
+        lzref_parse_chunk_mode(chunk, k, S, W, m, M, mode, tok_len, tok_off);
 
     if (c % REF_INDEX_STRIDE == 0)
       ref_put_u64(out + index_at + 8u * (c / REF_INDEX_STRIDE),
@@ -182,6 +265,20 @@ int lzref_compress(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
     uint64_t payload = 0;
     for (uint32_t t = 0; t < ntok; ++t)
       payload += tok_off[t] ? 1u + offB : S;
+
+    /* version 2: a chunk whose coded record would not be smaller than its
+     * bytes is stored as they are, marked by a token count of 0 */
+    if (version == 2 && flag_bytes + payload >= bytes) {
+      ref_put_u32(out + table_at + REF_TABLE_ENTRY * c, 0);
+      ref_put_u32(out + table_at + REF_TABLE_ENTRY * c + 4, (uint32_t)bytes);
+      if (pos + bytes > cap) {
+        rc = REF_ESMALL;
+        break;
+      }
+      memcpy(out + pos, chunk, (size_t)bytes);
+      pos += bytes;
+      continue;
+    }
     ref_put_u32(out + table_at + REF_TABLE_ENTRY * c, ntok);
     ref_put_u32(out + table_at + REF_TABLE_ENTRY * c + 4, (uint32_t)payload);
 
@@ -221,7 +318,7 @@ static int ref_read_header(const uint8_t *in, uint64_t in_bytes,
                            uint32_t *W, uint32_t *m, uint32_t *M,
                            uint64_t *nc, uint64_t *n) {
   if (in_bytes < REF_HEADER_BYTES) return REF_ECORRUPT;
-  if (memcmp(in, "GLZ1", 4) != 0 || in[4] != 1) return REF_ECORRUPT;
+  if (memcmp(in, "GLZ1", 4) != 0 || (in[4] != 1 && in[4] != 2)) return REF_ECORRUPT;
   if (in[9] || in[10] || in[11]) return REF_ECORRUPT;
   *S = in[5];
   *offB = in[6];
@@ -278,6 +375,12 @@ int lzref_decompress(const uint8_t *in, uint64_t in_bytes, uint8_t *out,
     uint8_t *dst = out + c * (uint64_t)C;
     uint64_t bytes = (c + 1 < nc) ? C : n - c * (uint64_t)C;
     uint32_t k = (uint32_t)(bytes / S);
+    if (ntok == 0 && in[4] == 2) { /* a stored chunk: its bytes as they are */
+      if (payload != bytes) return REF_ECORRUPT;
+      memcpy(dst, pay, (size_t)bytes);
+      pos += payload;
+      continue;
+    }
     uint32_t p = 0;
     for (uint32_t t = 0; t < ntok; ++t) {
       if (p >= k) return REF_ECORRUPT;

@@ -52,6 +52,19 @@ void lzref_longest_match(const uint8_t *chunk, uint32_t k, uint32_t p,
                          uint32_t S, uint32_t W, uint32_t M,
                          uint32_t *len, uint32_t *off);
 
+/* The paper's matcher at symbol p (section 3.3.2, its four matching
+ * steps): a forward scan of the window with a search pointer that is never
+ * moved back, see lzref.c.  Writes the length of the first longest run it
+ * meets (0 if none) and that run's offset.  Length <= offset, <= M and <=
+ * k - p, as for lzref_longest_match, which it never exceeds. */
+void lzref_paper_match(const uint8_t *chunk, uint32_t k, uint32_t p,
+                       uint32_t S, uint32_t W, uint32_t M, uint32_t *len,
+                       uint32_t *off);
+
+/* Matchers of the greedy parse. */
+#define LZREF_MATCH_EXACT 0u /* lzref_longest_match (the definition) */
+#define LZREF_MATCH_PAPER 1u /* lzref_paper_match (the paper's method) */
+
 /* Greedy parse of one chunk.  tok_len[t] = symbols covered by token t,
  * tok_off[t] = pointer offset in symbols (0 for a literal).  Arrays must
  * hold k entries.  Returns the number of tokens. */
@@ -59,11 +72,35 @@ uint32_t lzref_parse_chunk(const uint8_t *chunk, uint32_t k, uint32_t S,
                            uint32_t W, uint32_t m, uint32_t M,
                            uint32_t *tok_len, uint32_t *tok_off);
 
+uint32_t lzref_parse_chunk_mode(const uint8_t *chunk, uint32_t k, uint32_t S,
+                                uint32_t W, uint32_t m, uint32_t M,
+                                uint32_t mode, uint32_t *tok_len,
+                                uint32_t *tok_off);
+
 int lzref_compress(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
                    uint32_t W, uint32_t m, uint32_t M, uint8_t *out,
                    uint64_t cap, uint64_t *out_bytes);
 
-/* Reads n_bytes from a header; 0 ok, 3 corrupt. */
+/* lzref_compress with the matcher `mode` (LZREF_MATCH_*); the stream
+ * layout does not depend on it. */
+int lzref_compress_mode(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
+                        uint32_t W, uint32_t m, uint32_t M, uint32_t mode,
+                        uint8_t *out, uint64_t cap, uint64_t *out_bytes);
+
+/* lzref_compress_mode writing stream version `version`:
+ *   1  the layout above;
+ *   2  the same layout (version byte 2) in which a chunk whose coded record
+ *      (flag bytes + payload) would be at least as large as the chunk
+ *      itself is stored instead: table entry {0, chunk bytes}, record =
+ *      the chunk's bytes (no flags).  A coded chunk always has >= 1 token,
+ *      so a token count of 0 marks a stored chunk unambiguously.
+ * The decoder reads both versions. */
+int lzref_compress_v(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
+                     uint32_t W, uint32_t m, uint32_t M, uint32_t mode,
+                     uint32_t version, uint8_t *out, uint64_t cap,
+                     uint64_t *out_bytes);
+
+/* Reads n_bytes from a header (version 1 or 2); 0 ok, 3 corrupt. */
 int lzref_decompressed_size(const uint8_t *in, uint64_t in_bytes,
                             uint64_t *n);
 

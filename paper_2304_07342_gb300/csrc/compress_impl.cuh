@@ -5,7 +5,10 @@
 // III (deflate, 3.3.4).  Here all of it is one persistent kernel; each warp
 // takes the next chunk from a work counter and
 //   1. stages the chunk into its shared-memory slice (1-D TMA bulk copy);
-//   2. links every position to the last earlier position with the same
+//   2. checks whether any position can start a match at all (a Bloom
+//      filter over symbol keys; chunks without repeats end here as all
+//      literals), else
+//      links every position to the last earlier position with the same
 //      hash of its first min(m, 8/S) symbols (hash chains; __match_any_sync
 //      links positions of one 32-position slab) and marks the positions
 //      whose chain reaches into the window -- only those can start a match
@@ -13,7 +16,8 @@
 //   3. walks the greedy parse (section 2.2 steps 1-6): the next 32 marked
 //      positions are evaluated in parallel, one lane each, by walking their
 //      chains nearest-first and extending every candidate exactly (length
-//      <= offset, section 3.3.2); the parse through the batch is found by a
+//      <= offset, section 3.3.2) -- or, in the paper's matcher mode, by
+//      the paper's forward scan of the window -- the parse through the batch is found by a
 //      short chase over lanes, then warp scans give each token its index
 //      and payload offset (the local, first pass of the two-pass prefix sum
 //      of section 3.2.2) and the lanes write the tokens in parallel into a
@@ -226,6 +230,7 @@ __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
 // lie in one slab and p came second, in which case p is flagged and (ii)
 // finds it.
 constexpr uint32_t kBloomMaxFlagged = 16;
+constexpr uint32_t kBloomGroup = 8;  // slabs whose ORs are issued together
 
 // Does p (flagged, p + m <= k) take part in a match of >= m symbols, as the
 // position coded ((i)) or as the source of a later position of its slab
@@ -263,22 +268,36 @@ __device__ __forceinline__ bool literal_chunk(const typename SymType<S>::T *sym,
   const uint32_t wshift = 32u - bl;
   const uint32_t nslab = (k + 31) / 32;
   uint32_t nflag = 0;
-  for (uint32_t s = 0; s < nslab; ++s) {
-    const uint32_t p = s * 32 + lane;
-    const bool ok = p + A.m <= k;
-    uint32_t lo = 0, hi = 0;
-    if (ok) key_at<S>(in, p, mlo, mhi, lo, hi);
-    const uint32_t h = ((hi * 0x85EBCA77u) ^ lo) * 0x9E3779B1u;
-    const uint32_t g = h * 0xC2B2AE3Du;
-    const uint32_t mask =
-        (1u << (g >> 27)) | (1u << ((g >> 22) & 31u)) | (1u << ((g >> 17) & 31u));
-    uint32_t old = 0;
-    if (ok) old = atomicOr(&bm[h >> wshift], mask);
-    const uint32_t f = __ballot_sync(kFull, ok && (old & mask) == mask);
-    if (lane == 0) maybe[s] = f;
-    nflag += __popc(f);
+  // groups of kBloomGroup slabs: keys and masks first, then the ORs in slab
+  // order (each behind the previous one), then the votes, so that the ORs of
+  // a group are in flight together
+  for (uint32_t s0 = 0; s0 < nslab; s0 += kBloomGroup) {
+    uint32_t widx[kBloomGroup], mask[kBloomGroup], old[kBloomGroup];
+    bool okk[kBloomGroup];
+#pragma unroll
+    for (uint32_t u = 0; u < kBloomGroup; ++u) {
+      const uint32_t p = (s0 + u) * 32 + lane;
+      const bool ok = s0 + u < nslab && p + A.m <= k;
+      uint32_t lo = 0, hi = 0;
+      if (ok) key_at<S>(in, p, mlo, mhi, lo, hi);
+      const uint32_t h = ((hi * 0x85EBCA77u) ^ lo) * 0x9E3779B1u;
+      const uint32_t g = h * 0xC2B2AE3Du;
+      widx[u] = h >> wshift;
+      mask[u] = (1u << (g >> 27)) | (1u << ((g >> 22) & 31u)) | (1u << ((g >> 17) & 31u));
+      okk[u] = ok;
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < kBloomGroup; ++u) {
+      old[u] = okk[u] ? atomicOr(&bm[widx[u]], mask[u]) : 0u;
+      __syncwarp();  // slab u's ORs before slab u+1's
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < kBloomGroup; ++u) {
+      const uint32_t f = __ballot_sync(kFull, okk[u] && (old[u] & mask[u]) == mask[u]);
+      if (lane == 0 && s0 + u < nslab) maybe[s0 + u] = f;
+      nflag += __popc(f);
+    }
     if (nflag > kBloomMaxFlagged) return false;
-    __syncwarp();  // this slab's ORs before the next slab's
   }
   __syncwarp();
   if (nflag == 0) return true;
@@ -370,6 +389,63 @@ __device__ __forceinline__ bool chain_match(const typename SymType<S>::T *sym,
     d += step;
   }
   return true;
+}
+
+// First position w' in [w, p) with sym[w'] == c, or p if there is none.
+// One aligned 32-bit word (4/S symbols) per step for S < 4.
+template <int S>
+__device__ __forceinline__ uint32_t next_equal(const typename SymType<S>::T *sym, uint32_t w,
+                                               uint32_t p, typename SymType<S>::T c) {
+  if constexpr (S == 4) {
+    while (w < p && sym[w] != c) ++w;
+    return w;
+  } else {
+    constexpr uint32_t per = 4 / S;
+    const uint32_t *w32 = reinterpret_cast<const uint32_t *>(sym);
+    const uint32_t rep = S == 1 ? 0x01010101u * c : 0x00010001u * c;
+    while (w < p) {
+      const uint32_t first = w & ~(per - 1);  // first symbol of w's word
+      uint32_t eq = S == 1 ? __vcmpeq4(w32[first / per], rep) : __vcmpeq2(w32[first / per], rep);
+      eq &= kFull << (8u * S * (w - first));  // symbols before w do not count
+      if (eq) return min(p, first + static_cast<uint32_t>(__ffs(eq) - 1) / (8u * S));
+      w = first + per;
+    }
+    return p;
+  }
+}
+
+// The paper's matcher at position p (section 3.3.2, the four steps of its
+// matching method), one lane per position.  The search pointer starts at
+// the window start; at a symbol equal to the one at p a run starts and both
+// pointers advance while the symbols agree; at a mismatch the run is kept
+// if strictly longer than the best, the position pointer returns to p and
+// the search pointer moves on from the symbol that broke the run (it never
+// goes back).  The scan ends when a run reaches p (length <= offset) or the
+// end of the look-ahead (the chunk end or M symbols, whichever is first).
+// Here the search pointer jumps straight to the next symbol equal to the
+// one at p, and each run is measured four bytes at a time; the visited runs
+// are the same.  Ties keep the first run found (the farthest offset).
+template <int S>
+__device__ __forceinline__ void paper_match(const typename SymType<S>::T *sym, uint32_t k,
+                                            const BufDesc &A, uint32_t p, uint32_t &best,
+                                            uint32_t &bd) {
+  const uint32_t end = min(k, p + A.M);
+  const auto c = sym[p];
+  best = 0;
+  bd = 0;
+  uint32_t w = p > A.W ? p - A.W : 0;
+  while (true) {
+    w = next_equal<S>(sym, w, p, c);
+    if (w >= p) break;
+    const uint32_t cap = min(p - w, end - p);
+    const uint32_t l = extend_words<S>(reinterpret_cast<const uint8_t *>(sym), p, p - w, cap);
+    if (l > best) {
+      best = l;
+      bd = p - w;
+    }
+    if (l == cap) break;  // the run reached p or the look-ahead end
+    w += l + 1;
+  }
 }
 
 // Exact longest match at p by the whole warp (fallback for positions whose
@@ -521,7 +597,10 @@ __device__ __forceinline__ void greedy_walk(const typename SymType<S>::T *sym,
     const bool valid = lane < nvalid;
     uint32_t L = 0, bd = 0;
     bool resolved = true;
-    if (valid) resolved = chain_match<S, WIDE>(sym, k, A, links, mypos, L, bd);
+    if (valid) {
+      if (A.match == kMatchPaper) paper_match<S>(sym, k, A, mypos, L, bd);
+      else resolved = chain_match<S, WIDE>(sym, k, A, links, mypos, L, bd);
+    }
     const uint32_t unres = __ballot_sync(kFull, !resolved);
     uint32_t nxt = valid ? mypos + (L >= A.m ? L : 1u) : k;
     uint32_t succ = count_below(mypos, nxt);
@@ -636,6 +715,7 @@ constexpr unsigned long long kPrefix = 1ull << 63, kAgg = 1ull << 62;
 constexpr unsigned long long kVal = kAgg - 1;
 constexpr uint32_t kLookbackRounds = 8;  // windows of 32 per attempt
 constexpr uint32_t kFreeSlot = 0xFFFFFFFFu;
+constexpr uint32_t kLiteralRef = 1u << 31;  // parked record = zero flags + the input chunk
 
 __device__ __forceinline__ void publish(unsigned long long *status, uint32_t c,
                                         unsigned long long flag, uint64_t v,
@@ -687,9 +767,22 @@ __device__ __forceinline__ bool lookback_wait(const unsigned long long *status,
   return false;
 }
 
+// n zero bytes at dst (any alignment), by the warp.
+__device__ __forceinline__ void warp_zero(uint8_t *dst, uint32_t n, uint32_t lane) {
+  const uint32_t head =
+      min(n, (4u - static_cast<uint32_t>(reinterpret_cast<uintptr_t>(dst) & 3u)) & 3u);
+  if (lane < head) dst[lane] = 0;
+  const uint32_t words = (n - head) >> 2;
+  uint32_t *d32 = reinterpret_cast<uint32_t *>(dst + head);
+  for (uint32_t j = lane; j < words; j += 32) d32[j] = 0;
+  const uint32_t done = head + 4u * words;
+  if (lane < n - done) dst[done + lane] = 0;
+}
+
 // Step 5 for a chunk whose global offset is known: publish its inclusive
 // prefix, its index entry (every 64th chunk), the stream size (last chunk)
-// and copy its record (from shared staging or a parking slot).
+// and copy its record (from shared staging or a parking slot; src1 ==
+// nullptr writes n1 zero bytes).
 __device__ __forceinline__ void place_record(const CompressArgs &A, const BufDesc &B,
                                              uint32_t c, uint64_t excl, uint64_t rec,
                                              const uint8_t *src1, uint32_t n1,
@@ -709,7 +802,8 @@ __device__ __forceinline__ void place_record(const CompressArgs &A, const BufDes
     return;
   }
   uint8_t *o = B.out + dst;
-  warp_copy(o, src1, n1, lane);
+  if (src1) warp_copy(o, src1, n1, lane);
+  else warp_zero(o, n1, lane);
   if (n2) warp_copy(o + n1, src2, n2, lane);
 }
 
@@ -745,8 +839,17 @@ __device__ __forceinline__ void drain_parked(const CompressArgs &A, WarpState &W
       data_ok = lookback_wait(A.status + B.gbase, cs, lane, A.err, excl);
     }
     if (!ok) continue;
-    const uint8_t *slot = W.slots + static_cast<uint64_t>(sidx) * A.park_slot_bytes;
-    place_record(A, B, cs, excl, rs, slot, rs, nullptr, 0, data_ok, lane);
+    if (rs & kLiteralRef) {
+      // a record made of the chunk's own input bytes after zero flag bytes
+      // (all literals), or of those bytes alone (a stored chunk)
+      const uint32_t bytes = (cs + 1 < B.nc) ? B.C : static_cast<uint32_t>(B.n - uint64_t(cs) * B.C);
+      const uint32_t rec = rs & ~kLiteralRef;
+      place_record(A, B, cs, excl, rec, nullptr, rec - bytes,
+                   B.in + static_cast<uint64_t>(cs) * B.C, bytes, data_ok, lane);
+    } else {
+      const uint8_t *slot = W.slots + static_cast<uint64_t>(sidx) * A.park_slot_bytes;
+      place_record(A, B, cs, excl, rs, slot, rs, nullptr, 0, data_ok, lane);
+    }
     if (lane == sidx) W.slot_c = kFreeSlot;
     __syncwarp();
   }
@@ -782,7 +885,7 @@ __device__ __forceinline__ void write_header(const BufDesc &B, uint32_t lane) {
     case 1: b = 'L'; break;
     case 2: b = 'Z'; break;
     case 3: b = '1'; break;
-    case 4: b = 1; break;
+    case 4: b = B.version == 2 ? 2u : 1u; break;
     case 5: b = B.S; break;
     case 6: b = B.offB; break;
     case 7: b = B.m; break;
@@ -863,7 +966,15 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
     payload = W.pay;
   }
   if (!sane && lane == 0) atomicOr(A.err, kErrInternal);
-  const uint32_t fb = (ntok + 7) / 8;
+  uint32_t fb = (ntok + 7) / 8;
+  if (B.version == 2 && fb + pb >= bytes) {
+    // stream version 2: a record that would not be smaller than the chunk is
+    // replaced by the chunk's bytes, marked by a token count of 0
+    ntok = 0;
+    fb = 0;
+    pb = bytes;
+    payload = W.inb;
+  }
   const uint64_t rec = static_cast<uint64_t>(fb) + pb;
 
   // 4. global offset: publish the aggregate at once, so that no other
@@ -885,13 +996,19 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
         __ballot_sync(kFull, lane < A.park_slots && W.slot_c == kFreeSlot);
     if (free_mask && data_ok) {
       const uint32_t sidx = __ffs(free_mask) - 1;
-      uint8_t *slot = W.slots + static_cast<uint64_t>(sidx) * A.park_slot_bytes;
-      warp_copy(slot, W.flags, fb, lane);
-      warp_copy(slot + fb, payload, pb, lane);
+      // a record of zero flags and the chunk's input (all literals), or of
+      // the input alone (stored), is parked by reference
+      // (not the last chunk: a copy may read up to 3 bytes past its source)
+      const bool by_ref = payload == W.inb && c + 1 < B.nc;
+      if (!by_ref) {
+        uint8_t *slot = W.slots + static_cast<uint64_t>(sidx) * A.park_slot_bytes;
+        warp_copy(slot, W.flags, fb, lane);
+        warp_copy(slot + fb, payload, pb, lane);
+      }
       if (lane == sidx) {
         W.slot_c = c;
         W.slot_item = item;
-        W.slot_rec = static_cast<uint32_t>(rec);
+        W.slot_rec = static_cast<uint32_t>(rec) | (by_ref ? kLiteralRef : 0u);
       }
     } else {
       const bool ok = lookback_wait(status, c, lane, A.err, excl);

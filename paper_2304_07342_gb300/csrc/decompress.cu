@@ -33,14 +33,15 @@ namespace glz {
 namespace {
 
 struct Header {
-  uint32_t S, offB, m, M, C, W, nc;
+  uint32_t version, S, offB, m, M, C, W, nc;
   uint64_t n;
 };
 
 __device__ __forceinline__ bool read_header(const uint8_t *in, Header &h) {
   const bool magic = in[0] == 'G' && in[1] == 'L' && in[2] == 'Z' &&
-                     in[3] == '1' && in[4] == 1 && in[9] == 0 && in[10] == 0 &&
-                     in[11] == 0;
+                     in[3] == '1' && (in[4] == 1 || in[4] == 2) && in[9] == 0 &&
+                     in[10] == 0 && in[11] == 0;
+  h.version = in[4];
   h.S = in[5];
   h.offB = in[6];
   h.m = in[7];
@@ -175,8 +176,11 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
   const uint64_t chunk_at = static_cast<uint64_t>(c) * h.C;
   const uint32_t k = static_cast<uint32_t>(
       ((c + 1 < h.nc) ? h.C : h.n - chunk_at) / h.S);
+  // version 2: a token count of 0 marks a stored chunk (its bytes as they are)
+  const bool stored = h.version == 2 && ntok == 0;
   bad = bad || idxv > A.in_bytes || rec_at + fb + pay > A.in_bytes ||
-        rec_at + fb + pay < rec_at || ntok > k || (ntok == 0 && k > 0) ||
+        rec_at + fb + pay < rec_at || ntok > k || (ntok == 0 && k > 0 && !stored) ||
+        (stored && static_cast<uint64_t>(pay) != static_cast<uint64_t>(k) * h.S) ||
         fb + pay > record_bound(k, h);
   if (bad) {
     if (lane == 0) atomicOr(A.err, kErrCorrupt);
@@ -194,6 +198,14 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
   }
   const uint8_t *payload = flags + fb;
   uint8_t *dst = A.out + chunk_at;
+  if (stored) {
+    if (win) {
+      copy_s2g(dst, payload, pay, lane);  // the window has slack past the record
+    } else {
+      for (uint32_t i = lane; i < pay; i += 32) dst[i] = payload[i];
+    }
+    return true;
+  }
   const uint32_t S = h.S, offB = h.offB, tsz = 1 + h.offB;
   if (win) {
     // a chunk without pointers is its payload: copy it straight out

@@ -243,7 +243,17 @@ void lz_destroy(lz_ctx *ctx) {
 lz_status lz_compress(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
                       const lz_params *p, void *d_out, uint64_t out_cap,
                       uint64_t *d_out_bytes, lz_stream_t stream) {
+  return lz_compress_ex(ctx, d_in, n_bytes, p, nullptr, d_out, out_cap, d_out_bytes, stream);
+}
+
+lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
+                         const lz_params *p, const lz_options *opt, void *d_out,
+                         uint64_t out_cap, uint64_t *d_out_bytes, lz_stream_t stream) {
   if (!ctx || !params_ok(p) || !d_out || !d_out_bytes) return LZ_ERR_INVALID_ARG;
+  const uint32_t match = opt ? opt->match : LZ_MATCH_EXACT;
+  const uint32_t version = opt && opt->version ? opt->version : 1u;
+  if (match != LZ_MATCH_EXACT && match != LZ_MATCH_PAPER) return LZ_ERR_INVALID_ARG;
+  if (version != 1 && version != 2) return LZ_ERR_INVALID_ARG;
   if (n_bytes > 0 && !d_in) return LZ_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(d_out_bytes) % 8 != 0) return LZ_ERR_INVALID_ARG;
   const uint32_t S = p->symbol_bytes, C = p->chunk_bytes;
@@ -308,6 +318,8 @@ lz_status lz_compress(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
   A.buf.nc = static_cast<uint32_t>(nc);
   A.buf.records_at = records_at;
   A.buf.in_aligned = (reinterpret_cast<uintptr_t>(d_in) % 16) == 0;
+  A.buf.match = match == LZ_MATCH_PAPER ? glz::kMatchPaper : glz::kMatchExact;
+  A.buf.version = version;
   A.buf.gbase = 0;
   A.total_chunks = nc;
   A.sm = sm;
@@ -345,7 +357,7 @@ lz_status lz_decompressed_size(const void *d_in, uint64_t in_bytes,
   uint64_t n = 0;
   for (int i = 0; i < 8; ++i) n |= static_cast<uint64_t>(h[24 + i]) << (8 * i);
   lz_params p{h[5], u32(12), u32(16), h[7], h[8]};
-  if (std::memcmp(h, "GLZ1", 4) != 0 || h[4] != 1 || h[9] || h[10] || h[11] ||
+  if (std::memcmp(h, "GLZ1", 4) != 0 || (h[4] != 1 && h[4] != 2) || h[9] || h[10] || h[11] ||
       !params_ok(&p) || h[6] != off_bytes(p.window) || n % p.symbol_bytes != 0 ||
       u32(20) != div_up(n, p.chunk_bytes))
     return LZ_ERR_CORRUPT;
@@ -811,7 +823,7 @@ lz_status batch_create_decompress(lz_ctx *ctx, const lz_batch_item *items, uint3
                 static_cast<uint32_t>(header_u(h, 16, 4)), h[7], h[8]};
     const uint64_t nn = header_u(h, 24, 8);
     const uint64_t nc = header_u(h, 20, 4);
-    if (std::memcmp(h, "GLZ1", 4) != 0 || h[4] != 1 || h[9] || h[10] || h[11] ||
+    if (std::memcmp(h, "GLZ1", 4) != 0 || (h[4] != 1 && h[4] != 2) || h[9] || h[10] || h[11] ||
         !params_ok(&p) || h[6] != off_bytes(p.window) || nn % p.symbol_bytes != 0 ||
         nc != div_up(nn, p.chunk_bytes))
       return LZ_ERR_CORRUPT;
@@ -958,12 +970,23 @@ lz_status lz_autotune(lz_ctx *ctx, const void *d_sample, uint64_t sample_bytes,
     t.ratio = size ? static_cast<double>(sample_bytes) / size : 0.0;
   }
   if (s == LZ_OK) {
-    // the fastest set whose ratio is within 2% of the best ratio seen
+    // among the sets whose ratio is within 2% of the best ratio seen, the
+    // smallest chunk that is within 10% of the fastest time (a smaller chunk
+    // needs less shared memory per warp, which matters when buffers of other
+    // kinds share a batched launch), the fastest among those
     double best_ratio = 0;
     for (const Trial &t : trials) best_ratio = std::max(best_ratio, t.ratio);
-    const Trial *pick = nullptr;
+    double fastest = 0;
     for (const Trial &t : trials)
-      if (t.ratio >= 0.98 * best_ratio && (!pick || t.seconds < pick->seconds)) pick = &t;
+      if (t.ratio >= 0.98 * best_ratio && (fastest == 0 || t.seconds < fastest))
+        fastest = t.seconds;
+    const Trial *pick = nullptr;
+    for (const Trial &t : trials) {
+      if (t.ratio < 0.98 * best_ratio || t.seconds > 1.1 * fastest) continue;
+      if (!pick || t.p.chunk_bytes < pick->p.chunk_bytes ||
+          (t.p.chunk_bytes == pick->p.chunk_bytes && t.seconds < pick->seconds))
+        pick = &t;
+    }
     *out = pick->p;
   }
   if (e0) cudaEventDestroy(e0);
@@ -971,6 +994,55 @@ lz_status lz_autotune(lz_ctx *ctx, const void *d_sample, uint64_t sample_bytes,
   if (d_out) cudaFree(d_out);
   if (d_nb) cudaFree(d_nb);
   return s;
+}
+
+// Parameter policy (section 3.2.3): multi-byte matching first, with the
+// level's window enlarged S times; single-byte matching with the level's
+// window when the sample's compression ratio is below 1.5.
+static uint32_t min_profitable_match(uint32_t S, uint32_t W) {
+  return (1u + off_bytes(W)) / S + 1u;
+}
+
+lz_status lz_select_params(lz_ctx *ctx, const void *d_sample, uint64_t sample_bytes,
+                           uint32_t dtype_bytes, uint32_t level, uint32_t chunk_bytes,
+                           lz_params *out, lz_stream_t stream) {
+  static const uint32_t kLevelWindow[4] = {32, 64, 128, 255};
+  if (!ctx || !out) return LZ_ERR_INVALID_ARG;
+  if (dtype_bytes != 1 && dtype_bytes != 2 && dtype_bytes != 4) return LZ_ERR_INVALID_ARG;
+  if (level < 1 || level > 4) return LZ_ERR_INVALID_ARG;
+  const uint32_t Wl = kLevelWindow[level - 1];
+  const lz_params single{1, chunk_bytes, Wl, min_profitable_match(1, Wl), 255};
+  if (!params_ok(&single)) return LZ_ERR_INVALID_ARG;
+  if (dtype_bytes == 1) {
+    *out = single;
+    return LZ_OK;
+  }
+  sample_bytes -= sample_bytes % dtype_bytes;
+  if (sample_bytes == 0 || !d_sample) return LZ_ERR_INVALID_ARG;
+  const uint32_t Wm = std::min<uint32_t>(glz::kMaxWindow, dtype_bytes * Wl);
+  const lz_params multi{dtype_bytes, chunk_bytes, Wm, min_profitable_match(dtype_bytes, Wm), 255};
+  const uint64_t cap = lz_compressed_bound(sample_bytes, &multi);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  void *d_out = nullptr, *d_nb = nullptr;
+  lz_status s = LZ_OK;
+  if (cudaMallocAsync(&d_out, cap, st) != cudaSuccess ||
+      cudaMallocAsync(&d_nb, 8, st) != cudaSuccess)
+    s = LZ_ERR_NOMEM;
+  if (s == LZ_OK)
+    s = lz_compress(ctx, d_sample, sample_bytes, &multi, d_out, cap,
+                    static_cast<uint64_t *>(d_nb), stream);
+  uint64_t size = 0;
+  if (s == LZ_OK && cudaMemcpyAsync(&size, d_nb, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    s = LZ_ERR_CUDA;
+  if (d_out) cudaFreeAsync(d_out, st);
+  if (d_nb) cudaFreeAsync(d_nb, st);
+  const lz_status sync = lz_sync(ctx, stream);
+  if (s == LZ_OK) s = sync;
+  if (s != LZ_OK) return s;
+  // ratio n / size below 3/2, in integers
+  *out = (2 * sample_bytes < 3 * size) ? single : multi;
+  return LZ_OK;
 }
 
 }  // extern "C"

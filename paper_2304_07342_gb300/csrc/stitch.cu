@@ -29,7 +29,7 @@ __device__ __forceinline__ uint32_t ld_u32_le(const uint8_t *p) {
 // that splits the whole input into total_chunks chunks.
 __device__ bool shard_header_ok(const StitchArgs &A) {
   const uint8_t *h = A.shard;
-  if (ld_u32_le(h) != 0x315A4C47u || h[4] != 1) return false;  // "GLZ1", version 1
+  if (ld_u32_le(h) != 0x315A4C47u || (h[4] != 1 && h[4] != 2)) return false;  // "GLZ1", v1/v2
   const uint32_t C = ld_u32_le(h + 12);
   if (C < 16 || C > kMaxChunk || C % 16 != 0) return false;
   const uint64_t nc = ld_u32_le(h + 20), n = ld_u64_le(h + 24);

@@ -24,15 +24,19 @@ LZ_ERR_CUDA = 5
 LZ_ERR_TIMEOUT = 6
 LZ_ERR_INTERNAL = 7
 
+LZ_MATCH_EXACT = 0  # longest match, nearest offset on ties (the definition)
+LZ_MATCH_PAPER = 1  # the paper's forward scan (section 3.3.2)
+
 _NAMES = {0: "LZ_OK", 1: "LZ_ERR_INVALID_ARG", 2: "LZ_ERR_BUFFER_TOO_SMALL",
           3: "LZ_ERR_CORRUPT", 4: "LZ_ERR_NOMEM", 5: "LZ_ERR_CUDA",
           6: "LZ_ERR_TIMEOUT", 7: "LZ_ERR_INTERNAL"}
 
 # every symbol include/lz.h declares
 EXPORTS = ("lz_create", "lz_destroy", "lz_status_string", "lz_check_params",
-           "lz_compressed_bound", "lz_compress", "lz_decompressed_size",
+           "lz_compressed_bound", "lz_compress", "lz_compress_ex", "lz_decompressed_size",
            "lz_decompress", "lz_sync", "lz_compress_noalloc", "lz_batch_create",
-           "lz_batch_run", "lz_batch_destroy", "lz_autotune", "lz_stitch")
+           "lz_batch_run", "lz_batch_destroy", "lz_autotune", "lz_stitch",
+           "lz_select_params")
 
 
 class LzError(RuntimeError):
@@ -45,6 +49,10 @@ class lz_params(ctypes.Structure):
     _fields_ = [("symbol_bytes", ctypes.c_uint32), ("chunk_bytes", ctypes.c_uint32),
                 ("window", ctypes.c_uint32), ("min_match", ctypes.c_uint32),
                 ("max_match", ctypes.c_uint32)]
+
+
+class lz_options(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_uint32), ("version", ctypes.c_uint32)]
 
 
 class lz_batch_item(ctypes.Structure):
@@ -92,6 +100,8 @@ def load(path: str = LIB_PATH):
     lib.lz_compressed_bound.restype = u64
     lib.lz_compress.argtypes = [vp, vp, u64, pp, vp, u64, vp, vp]
     lib.lz_compress.restype = i32
+    lib.lz_compress_ex.argtypes = [vp, vp, u64, pp, ctypes.POINTER(lz_options), vp, u64, vp, vp]
+    lib.lz_compress_ex.restype = i32
     lib.lz_decompressed_size.argtypes = [vp, u64, ctypes.POINTER(u64), vp]
     lib.lz_decompressed_size.restype = i32
     lib.lz_decompress.argtypes = [vp, vp, u64, vp, u64, vp, vp]
@@ -109,6 +119,9 @@ def load(path: str = LIB_PATH):
     lib.lz_batch_destroy.restype = None
     lib.lz_autotune.argtypes = [vp, vp, u64, ctypes.c_uint32, pp]
     lib.lz_autotune.restype = i32
+    u32 = ctypes.c_uint32
+    lib.lz_select_params.argtypes = [vp, vp, u64, u32, u32, u32, pp, vp]
+    lib.lz_select_params.restype = i32
     lib.lz_stitch.argtypes = [vp, vp, u64, u64, u64, u64, u64, u64, vp, u64, vp]
     lib.lz_stitch.restype = i32
     _lib = lib
@@ -148,6 +161,13 @@ def lz_compress(ctx: int, d_in: int, n_bytes: int, p: Params, d_out: int,
                 out_cap: int, d_out_bytes: int, stream: int = 0) -> None:
     _check(load().lz_compress(ctx, d_in, n_bytes, ctypes.byref(p.c()), d_out,
                               out_cap, d_out_bytes, stream), "lz_compress")
+
+
+def lz_compress_ex(ctx: int, d_in: int, n_bytes: int, p: Params, d_out: int, out_cap: int,
+                   d_out_bytes: int, stream: int = 0, match: int = 0, version: int = 1) -> None:
+    opt = lz_options(match, version)
+    _check(load().lz_compress_ex(ctx, d_in, n_bytes, ctypes.byref(p.c()), ctypes.byref(opt),
+                                 d_out, out_cap, d_out_bytes, stream), "lz_compress_ex")
 
 
 def lz_decompressed_size(d_in: int, in_bytes: int, stream: int = 0) -> int:
@@ -207,6 +227,16 @@ def lz_autotune(ctx: int, d_sample: int, sample_bytes: int, symbol_bytes: int) -
     return Params(out.symbol_bytes, out.chunk_bytes, out.window, out.min_match, out.max_match)
 
 
+def lz_select_params(ctx: int, d_sample: int, sample_bytes: int, dtype_bytes: int,
+                     level: int = 3, chunk_bytes: int = 4096, stream: int = 0) -> Params:
+    """Section 3.2.3 policy: multi-byte matching unless the sample's ratio
+    with it is below 1.5 (then single-byte); windows by level 1-4."""
+    out = lz_params()
+    _check(load().lz_select_params(ctx, d_sample, sample_bytes, dtype_bytes, level, chunk_bytes,
+                                   ctypes.byref(out), stream), "lz_select_params")
+    return Params(out.symbol_bytes, out.chunk_bytes, out.window, out.min_match, out.max_match)
+
+
 def lz_sync(ctx: int, stream: int = 0) -> int:
     """Return (and clear) the sticky device status; does not raise."""
     return load().lz_sync(ctx, stream)
@@ -248,7 +278,8 @@ class Codec:
     def _bytes_of(x):
         return x.contiguous().view(-1).view(__import__("torch").uint8)
 
-    def compress(self, x, p: Params, out=None, out_bytes=None, stream=None):
+    def compress(self, x, p: Params, out=None, out_bytes=None, stream=None,
+                 match: int = LZ_MATCH_EXACT, version: int = 1):
         torch = self.torch
         xb = self._bytes_of(x)
         cap = lz_compressed_bound(xb.numel(), p)
@@ -258,8 +289,9 @@ class Codec:
             out = torch.empty(cap, dtype=torch.uint8, device=xb.device)
         if out_bytes is None:
             out_bytes = torch.zeros(1, dtype=torch.int64, device=xb.device)
-        lz_compress(self.ctx, xb.data_ptr(), xb.numel(), p, out.data_ptr(),
-                    out.numel(), out_bytes.data_ptr(), self._stream(stream))
+        lz_compress_ex(self.ctx, xb.data_ptr(), xb.numel(), p, out.data_ptr(), out.numel(),
+                       out_bytes.data_ptr(), self._stream(stream), match=match,
+                       version=version)
         return out, out_bytes
 
     def decompress(self, stream_bytes, n_bytes: int | None = None, out=None,
@@ -281,8 +313,9 @@ class Codec:
     def sync(self, stream=None) -> int:
         return lz_sync(self.ctx, self._stream(stream))
 
-    def compress_sync(self, x, p: Params, stream=None):
-        out, nb = self.compress(x, p, stream=stream)
+    def compress_sync(self, x, p: Params, stream=None, match: int = LZ_MATCH_EXACT,
+                      version: int = 1):
+        out, nb = self.compress(x, p, stream=stream, match=match, version=version)
         st = self.sync(stream)
         if st != LZ_OK:
             raise LzError(st, "compress (device)")

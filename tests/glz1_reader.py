@@ -26,17 +26,20 @@ class Stream:
     records_at: int = 0
     record_offsets: list = field(default_factory=list)  # relative to records_at
     tokens: list = field(default_factory=list)     # per chunk [(len, off)]
+    stored: list = field(default_factory=list)     # per chunk: stored as is (version 2)
     total_bytes: int = 0
+    version: int = 1
 
 
 def read(buf: bytes) -> Stream:
     buf = bytes(buf)
     assert buf[:4] == b"GLZ1", "magic"
     ver, S, offB, m, M = buf[4], buf[5], buf[6], buf[7], buf[8]
-    assert ver == 1 and buf[9:12] == b"\0\0\0"
+    assert ver in (1, 2) and buf[9:12] == b"\0\0\0"
     C, W, nc = struct.unpack_from("<III", buf, 12)
     (n,) = struct.unpack_from("<Q", buf, 24)
     st = Stream(S, offB, m, M, C, W, nc, n)
+    st.version = ver
     pos = 32
     for c in range(nc):
         st.table.append(struct.unpack_from("<II", buf, pos))
@@ -49,6 +52,15 @@ def read(buf: bytes) -> Stream:
     for c in range(nc):
         ntok, pay = st.table[c]
         st.record_offsets.append(rel)
+        if ver == 2 and ntok == 0:  # stored chunk: its bytes, no flags
+            bytes_c = min(C, n - c * C)
+            assert pay == bytes_c, "stored chunk size"
+            assert len(buf[pos + rel: pos + rel + pay]) == pay, "truncated record"
+            st.tokens.append([])
+            st.stored.append(True)
+            rel += pay
+            continue
+        st.stored.append(False)
         fb = (ntok + 7) // 8
         rec = buf[pos + rel: pos + rel + fb + pay]
         assert len(rec) == fb + pay, "truncated record"

@@ -43,7 +43,7 @@ def test_corrupt_streams_rejected_like_the_oracle(codec):
     first = st.records_at
     cases = []
     b = bytearray(good); b[0] = ord("X"); cases.append(b)
-    b = bytearray(good); b[4] = 2; cases.append(b)
+    b = bytearray(good); b[4] = 3; cases.append(b)
     b = bytearray(good); b[6] = 2; cases.append(b)
     b = bytearray(good); b[20] = 9; cases.append(b)
     cases.append(good[:-1])
@@ -144,3 +144,21 @@ def test_invalid_arguments(codec):
             lz.lz_compress(codec.ctx, din, n, P, dout, 4096, dob)
         assert e.value.status == lz.LZ_ERR_INVALID_ARG
     assert codec.sync() == lz.LZ_OK
+
+
+def test_corrupt_version2_streams_rejected_like_the_oracle(codec):
+    """Stream version 2: a stored chunk whose size disagrees with the chunk,
+    and a token count of 0 in a version-1 stream, are corrupt on both sides."""
+    x = np.frombuffer(bytes(range(48)) + b"abcabcabcabcabca", np.uint8)  # 3 stored, 1 coded
+    P = oracle.Params(1, 16, 8, 3, 255)
+    good = bytearray(oracle.compress(x, P, version=2).tobytes())
+    assert _decode_status(codec, good) == lz.LZ_OK
+    st = glz1_reader.read(bytes(good))
+    assert st.stored == [True, True, True, False]
+    cases = []
+    b = bytearray(good); b[36] = 15; cases.append(b)   # stored size 15 != 16
+    b = bytearray(good); b[4] = 1; cases.append(b)     # token count 0 in version 1
+    for i, c in enumerate(cases):
+        assert oracle.decompress_status(bytes(c)) == oracle.ECORRUPT, i
+        assert _decode_status(codec, c) == lz.LZ_ERR_CORRUPT, i
+        assert _decode_status(codec, good) == lz.LZ_OK, i

@@ -1,0 +1,106 @@
+"""Stream version 2 (stored chunks) on the GPU: lz_compress_ex with version 2
+writes streams byte-identical to the oracle's version-2 streams (a chunk
+whose coded record would not be smaller than the chunk is stored as it is),
+with both matchers; the GPU decoder (single and batched) reads them, and
+reads the oracle's version-2 streams too."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import Params
+from paper_2304_07342_gb300 import lz, synth
+from tests import gpu_util as G
+from tests.test_gpu_parity import GRID, KINDS, make_input
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def codec():
+    c = G.codec()
+    yield c
+    c.close()
+
+
+def gpu_v2(codec, x: np.ndarray, P: Params, match: int = 0, in_offset: int = 0) -> np.ndarray:
+    d = G.to_dev(x, in_offset)
+    return codec.compress_sync(d, lz.Params(*P.tuple()), match=match, version=2).cpu().numpy()
+
+
+def check(codec, x, P, match=0, in_offset=0):
+    ref = oracle.compress(x, P, mode=match, version=2)
+    got = gpu_v2(codec, x, P, match, in_offset)
+    assert np.array_equal(got, ref), G.first_difference(got, ref)
+    assert np.array_equal(G.gpu_decompress(codec, got), x.view(np.uint8).reshape(-1))
+    return got
+
+
+@pytest.mark.parametrize("S,C,W,m,M", GRID)
+@pytest.mark.parametrize("kind", KINDS)
+def test_v2_param_grid(codec, S, C, W, m, M, kind):
+    P = Params(S, C, W, m, M)
+    n_sym = (4 * C + C // 2) // S
+    check(codec, make_input(kind, n_sym, S, seed=S * 31 + W), P)
+
+
+@pytest.mark.parametrize("S", [1, 2, 4])
+def test_v2_paper_matcher(codec, S):
+    P = Params(S, 4096, 128, 2 if S == 4 else 3, 255)
+    check(codec, make_input("mixed", 6 * 4096 // S + 3, S, seed=S), P, match=lz.LZ_MATCH_PAPER)
+
+
+def test_v2_field_is_stored_and_smaller(codec):
+    """The noisy float field at S=4: every chunk stored, so the stream is the
+    input plus header, table and index."""
+    x = synth.gaussian_field((16, 128, 256), seed=3)
+    P = Params(4, 8192, 256, 2, 255)
+    got = check(codec, x, P)
+    nc = x.nbytes // 8192
+    assert got.size == 32 + 8 * nc + 8 * ((nc + 63) // 64) + x.nbytes
+
+
+@pytest.mark.parametrize("offset", [1, 4, 8])
+def test_v2_misaligned_input(codec, offset):
+    P = Params(2, 4096, 128, 3, 255)
+    check(codec, make_input("mixed", 5 * 2048 + 77, 2, seed=offset), P, in_offset=offset)
+
+
+@pytest.mark.parametrize("out_offset", [0, 3])
+def test_v2_decode_oracle_streams(codec, out_offset):
+    for S, kind in ((1, "random"), (2, "mixed"), (4, "quant")):
+        P = Params(S, 2048, 200, 2, 100)
+        x = make_input(kind, 30_000 // S * 2, S, seed=S + 9)
+        s = oracle.compress(x, P, version=2)
+        back = G.gpu_decompress(codec, s, out_offset=out_offset)
+        assert np.array_equal(back, x.view(np.uint8))
+
+
+def test_v2_batched_decompress(codec):
+    """Version-2 streams decode through the batched launch too."""
+    xs = [make_input(k, 3000 + 517 * i, 2, seed=i) for i, k in enumerate(KINDS)]
+    P = Params(2, 2048, 128, 3, 255)
+    streams = [G.to_dev(oracle.compress(x, P, version=2)) for x in xs]
+    outs = [torch.empty(x.nbytes, dtype=torch.uint8, device="cuda") for x in xs]
+    nbs = [torch.zeros(1, dtype=torch.int64, device="cuda") for _ in xs]
+    items = [(s.data_ptr(), s.numel(), o.data_ptr(), o.numel(), nb.data_ptr(), None)
+             for s, o, nb in zip(streams, outs, nbs)]
+    st = torch.cuda.current_stream().cuda_stream
+    b = lz.lz_batch_create(codec.ctx, items, decompress=True, stream=st)
+    lz.lz_batch_run(codec.ctx, b, st)
+    lz.lz_batch_destroy(b, st)
+    assert codec.sync() == lz.LZ_OK
+    for x, o in zip(xs, outs):
+        assert np.array_equal(o.cpu().numpy(), x.view(np.uint8))
+
+
+def test_v2_unknown_version_rejected(codec):
+    d = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    out = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(lz.LzError):
+        lz.lz_compress_ex(codec.ctx, d.data_ptr(), 64, lz.Params(1, 64, 8, 2, 255),
+                          out.data_ptr(), out.numel(), nb.data_ptr(),
+                          torch.cuda.current_stream().cuda_stream, version=3)

@@ -54,6 +54,46 @@ def brute_parse(sym: list, W: int, m: int, M: int):
     return toks
 
 
+def paper_jump(sym: list, p: int, W: int, M: int):
+    """The paper's matcher (section 3.3.2) restated as jumps between run
+    starts instead of pointer steps.  E = the window positions holding
+    x[p].  The scan meets the smallest w in E and follows the run from w as
+    far as it goes (not into p, not past the look-ahead of min(M, k-p)
+    symbols).  Unless the run reached p or the look-ahead end, the scan goes
+    on at the smallest w in E beyond the symbol that broke the run (that
+    symbol itself is never tried as a start).  The first run of the
+    greatest length wins."""
+    k = len(sym)
+    lo, end = max(0, p - W), min(k, p + M)
+    E = [w for w in range(lo, p) if sym[w] == sym[p]]
+    best, best_d, after = 0, 0, lo
+    for w in E:
+        if w < after:
+            continue
+        l = 0
+        while w + l < p and p + l < end and sym[w + l] == sym[p + l]:
+            l += 1
+        if l > best:
+            best, best_d = l, p - w
+        if w + l == p or p + l == end:
+            break
+        after = w + l + 1
+    return best, best_d
+
+
+def jump_parse(sym: list, W: int, m: int, M: int):
+    toks, p = [], 0
+    while p < len(sym):
+        l, d = paper_jump(sym, p, W, M)
+        if l >= m:
+            toks.append((l, d))
+            p += l
+        else:
+            toks.append((1, 0))
+            p += 1
+    return toks
+
+
 def symbols(b: bytes, S: int) -> list:
     return [b[i:i + S] for i in range(0, len(b), S)]
 
@@ -82,6 +122,9 @@ def _load_fixture(path):
                        {"u8": np.uint8, "u16": np.uint16}[dt]).tobytes()
     chunks = []
     for part in spec["tokens"].split("|"):
+        if part.strip() == "stored":
+            chunks.append("stored")
+            continue
         toks = []
         for t in part.split():
             if t.startswith("L*"):
@@ -94,7 +137,8 @@ def _load_fixture(path):
         chunks.append(toks)
     stream = bytes.fromhex(spec["stream_hex"].replace(" ", "")) if "stream_hex" in spec else None
     mp = bytes.fromhex(spec["match_payload_hex"]) if "match_payload_hex" in spec else None
-    return P, data, chunks, stream, mp
+    mode = {"exact": oracle.MATCH_EXACT, "paper": oracle.MATCH_PAPER}[spec.get("mode", "exact")]
+    return P, data, chunks, stream, mp, mode, int(spec.get("version", "1"))
 
 
 FIXTURES = sorted(glob.glob(os.path.join(GOLDEN, "*.txt")))
@@ -102,23 +146,35 @@ FIXTURES = sorted(glob.glob(os.path.join(GOLDEN, "*.txt")))
 
 @pytest.mark.parametrize("path", FIXTURES, ids=[os.path.basename(f) for f in FIXTURES])
 def test_golden_fixture(path):
-    P, data, chunk_tokens, stream, match_payload = _load_fixture(path)
-    out = oracle.compress(np.frombuffer(data, np.uint8), P).tobytes()
+    P, data, chunk_tokens, stream, match_payload, mode, version = _load_fixture(path)
+    out = oracle.compress(np.frombuffer(data, np.uint8), P, mode=mode, version=version).tobytes()
     st = glz1_reader.read(out)
-    assert st.tokens == chunk_tokens
+    assert st.version == version
+    assert st.stored == [t == "stored" for t in chunk_tokens]
+    assert st.tokens == [[] if t == "stored" else t for t in chunk_tokens]
     if stream is not None:
         assert out == stream
     if match_payload is not None:
         assert match_payload in out
-    # the fixture's tokens are also what brute force says
+    # the fixture's tokens are also what brute force says; a stored chunk is
+    # one whose brute-force record would not be smaller than the chunk
+    parse = brute_parse if mode == oracle.MATCH_EXACT else jump_parse
+    offB = 1 if P.W <= 256 else 2
     for c, toks in enumerate(chunk_tokens):
         chunk = data[c * P.C:(c + 1) * P.C]
-        assert brute_parse(symbols(chunk, P.S), P.W, P.m, P.M) == toks
+        bf = parse(symbols(chunk, P.S), P.W, P.m, P.M)
+        if toks == "stored":
+            rec = (len(bf) + 7) // 8 + sum(1 + offB if d else P.S for _, d in bf)
+            assert version == 2 and rec >= len(chunk)
+            rec_at = st.records_at + st.record_offsets[c]
+            assert out[rec_at:rec_at + len(chunk)] == chunk
+        else:
+            assert bf == toks
     assert oracle.decompress(out).tobytes() == data
 
 
 def test_fixture_count():
-    assert len(FIXTURES) >= 6
+    assert len(FIXTURES) >= 9
 
 
 # --- brute force --------------------------------------------------------------
@@ -310,7 +366,7 @@ def test_decoder_rejects_corruption():
     assert oracle.decompress_status(bytes(good)) == 0
     cases = []
     b = bytearray(good); b[0] = ord("X"); cases.append(b)          # magic
-    b = bytearray(good); b[4] = 2; cases.append(b)                 # version
+    b = bytearray(good); b[4] = 3; cases.append(b)                 # version
     b = bytearray(good); b[6] = 2; cases.append(b)                 # offB vs W
     b = bytearray(good); b[20] = 9; cases.append(b)                # n_chunks
     cases.append(good[:-1])                                        # truncated
@@ -326,3 +382,184 @@ def test_decoder_rejects_corruption():
     b = bytearray(good); b[st.records_at - 8] = 1; cases.append(b)    # index
     for i, c in enumerate(cases):
         assert oracle.decompress_status(bytes(c)) == oracle.ECORRUPT, i
+
+
+# --- the paper's matcher (section 3.3.2), mode MATCH_PAPER --------------------
+
+@pytest.mark.parametrize("alpha", [1, 2, 3])
+def test_paper_match_exhaustive_tiny(alpha):
+    """Every sequence of up to 7 one-byte symbols over a small alphabet, every
+    position, several windows and caps: the oracle's pointer walk equals
+    the jump formulation."""
+    for n in range(1, 8):
+        for seq in itertools.product(range(alpha), repeat=n):
+            b = bytes(seq)
+            sym = symbols(b, 1)
+            for W, M in ((1, 255), (2, 3), (3, 2), (8, 255), (4, 1)):
+                for p in range(n):
+                    assert oracle.paper_match(b, p, 1, W, M) == paper_jump(sym, p, W, M), \
+                        (seq, p, W, M)
+
+
+@pytest.mark.parametrize("S", [1, 2, 4])
+def test_paper_parse_random_small(S):
+    """Random chunks over small alphabets (many partial runs, which is where
+    the scan skips candidates): whole parses equal the jump formulation."""
+    rng = np.random.default_rng(40 + S)
+    for trial in range(60):
+        k = int(rng.integers(1, 90))
+        alpha = int(rng.integers(1, 5))
+        W = int(rng.integers(1, 40))
+        M = int(rng.integers(1, 20))
+        m = int(rng.integers(1, M + 1))
+        x = rng.integers(0, alpha, k).astype({1: np.uint8, 2: np.uint16, 4: np.uint32}[S])
+        b = x.tobytes()
+        assert oracle.parse_chunk(b, S, W, m, M, mode=oracle.MATCH_PAPER) == \
+            jump_parse(symbols(b, S), W, m, M), (trial, k, alpha, W, M, m)
+
+
+def test_paper_constant_run_closed_form():
+    """All symbols equal: at p the scan starts at lo = max(0, p-W), the first
+    run never breaks and ends at p or at the look-ahead end, so the match is
+    length min(W, p, k-p, M) at offset min(W, p) (farthest, where the exact
+    matcher takes the nearest)."""
+    for S, k, W, M in ((2, 2048, 128, 255), (1, 300, 256, 255), (4, 97, 16, 5)):
+        b = np.full(k, 9, {1: np.uint8, 2: np.uint16, 4: np.uint32}[S]).tobytes()
+        for p in range(k):
+            L = min(W, p, k - p, M)
+            assert oracle.paper_match(b, p, S, W, M) == (L, min(W, p) if L else 0), (S, p)
+
+
+@pytest.mark.parametrize("q,W,M,k", [(1, 16, 255, 100), (3, 64, 255, 500), (7, 50, 20, 400),
+                                     (5, 5, 255, 60)])
+def test_paper_period_closed_form(q, W, M, k):
+    """x[i] = i mod q: the first window position holding x[p] is lo + ((p -
+    lo) mod q); its run never breaks, so the offset is the largest multiple
+    of q that is <= min(W, p) and the length is min(offset, k-p, M)."""
+    b = (np.arange(k) % q).astype(np.uint8).tobytes()
+    for p in range(k):
+        d = (min(W, p) // q) * q
+        L = min(d, k - p, M)
+        assert oracle.paper_match(b, p, 1, W, M) == ((L, d) if L else (0, 0)), p
+
+
+def test_paper_match_never_exceeds_exact_and_is_valid():
+    """Every run the scan keeps is a true match with length <= offset <=
+    min(W, p), <= M and <= k - p, and is never longer than the exact
+    longest match; on data with one distinct repeat the two agree."""
+    rng = np.random.default_rng(7)
+    shorter = 0
+    for trial in range(40):
+        k = int(rng.integers(20, 300))
+        x = rng.integers(0, int(rng.integers(2, 6)), k).astype(np.uint8)
+        W, M = int(rng.integers(1, 64)), int(rng.integers(1, 40))
+        b = x.tobytes()
+        for p in range(k):
+            l, d = oracle.paper_match(b, p, 1, W, M)
+            le, _ = oracle.longest_match(b, p, 1, W, M)
+            assert l <= le
+            shorter += l < le
+            if l:
+                assert 1 <= l <= d <= min(W, p) and l <= M and l <= k - p
+                assert b[p:p + l] == b[p - d:p - d + l]
+    assert shorter > 0  # the heuristic does miss longer matches
+    y = np.arange(200, dtype=np.uint8)
+    y[150:160] = y[40:50]
+    assert oracle.paper_match(y.tobytes(), 150, 1, 255, 255) == \
+        oracle.longest_match(y.tobytes(), 150, 1, 255, 255) == (10, 110)
+
+
+@pytest.mark.parametrize("S,C,W,m,M", [(1, 64, 16, 3, 255), (2, 4096, 128, 3, 255),
+                                       (4, 8192, 256, 2, 255), (1, 1024, 300, 2, 255)])
+def test_paper_round_trip(S, C, W, m, M):
+    """Streams parsed with the paper's matcher use the same layout and decode
+    with the same decoder."""
+    rng = np.random.default_rng(S + W)
+    x = np.repeat(rng.integers(0, 5, 3000), rng.integers(1, 6, 3000))[: 9000 // S * S]
+    x = x.astype({1: np.uint8, 2: np.uint16, 4: np.uint32}[S])
+    P = Params(S, C, W, m, M)
+    s = oracle.compress(x, P, mode=oracle.MATCH_PAPER)
+    assert np.array_equal(oracle.decompress(s), x.view(np.uint8))
+    assert s.size >= oracle.compress(x, P).size * 0.9  # comparable, usually larger
+    st = glz1_reader.read(s.tobytes())
+    assert sum(sum(l for l, _ in t) for t in st.tokens) == x.size
+
+
+# --- parameter policy (section 3.2.3) -----------------------------------------
+
+def test_policy_min_match_is_shortest_profitable():
+    """m is the smallest length whose pointer bytes (1 + offB) are fewer than
+    the literal bytes S * m it replaces: checked against that definition by
+    enumeration."""
+    for S in (1, 2, 4):
+        for W in (32, 255, 256, 257, 1020):
+            offB = 1 if W <= 256 else 2
+            m = next(l for l in range(1, 10) if 1 + offB < S * l)
+            assert oracle.min_profitable_match(S, W) == m
+
+
+def test_policy_ratio_test_is_exact():
+    assert not oracle.ratio_below(3, 2)        # exactly 1.5 keeps multi-byte
+    assert oracle.ratio_below(299, 200)        # 1.495
+    assert not oracle.ratio_below(301, 200)    # 1.505
+    assert oracle.ratio_below(10, 11)          # expansion
+
+
+def test_policy_decisions():
+    """One-byte data needs no trial; a constant field keeps 4-byte symbols
+    with the window enlarged 4x; noisy words (ratio < 1) fall back to
+    single bytes with the level's window; the trial is the oracle's own
+    stream size."""
+    assert oracle.select_params(np.arange(100, dtype=np.uint8), 1, 2) == Params(1, 4096, 64, 3, 255)
+    c = np.full(20_000, 9, np.uint32)
+    assert oracle.select_params(c, 4, 1) == Params(4, 4096, 128, 1, 255)
+    assert oracle.select_params(c, 4, 4) == Params(4, 4096, 1020, 1, 255)
+    r = np.random.default_rng(0).integers(0, 1 << 32, 20_000, dtype=np.uint64).astype(np.uint32)
+    assert oracle.select_params(r, 4, 3) == Params(1, 4096, 128, 3, 255)
+    x = np.repeat(np.arange(50, dtype=np.uint16), 40)
+    multi = Params(2, 4096, 256, 2, 255)
+    keep = not oracle.ratio_below(x.nbytes, oracle.compress(x, multi).size)
+    assert keep and oracle.select_params(x, 2, 3) == multi
+
+
+# --- stream version 2: stored chunks -------------------------------------------
+
+@pytest.mark.parametrize("S,C,W,m,M", [(1, 64, 16, 3, 255), (2, 4096, 128, 3, 255),
+                                       (4, 8192, 256, 2, 255), (1, 1024, 300, 2, 255),
+                                       (2, 16, 1, 1, 1)])
+def test_v2_stores_exactly_the_chunks_that_do_not_shrink(S, C, W, m, M):
+    """Version 2 keeps every coded record that is smaller than its chunk,
+    byte for byte as in version 1, and stores the others as they are; it is
+    never larger than version 1 and decodes to the input."""
+    rng = np.random.default_rng(S * 7 + C)
+    dt = {1: np.uint8, 2: np.uint16, 4: np.uint32}[S]
+    n_sym = (7 * C + C // 3) // S
+    parts = [rng.integers(0, 3, n_sym // 3), rng.integers(0, 1 << (8 * S), n_sym // 3, dtype=np.uint64),
+             np.repeat(rng.integers(0, 50, n_sym), 3)]
+    x = np.concatenate(parts)[:n_sym].astype(dt)
+    P = Params(S, C, W, m, M)
+    v1 = oracle.compress(x, P).tobytes()
+    v2 = oracle.compress(x, P, version=2).tobytes()
+    a, b = glz1_reader.read(v1), glz1_reader.read(v2)
+    assert len(v2) <= len(v1) and any(b.stored)
+    xb = x.tobytes()
+    for c in range(a.n_chunks):
+        ntok, pay = a.table[c]
+        raw = xb[c * C:(c + 1) * C]
+        if (ntok + 7) // 8 + pay >= len(raw):
+            assert b.stored[c] and b.table[c] == (0, len(raw))
+            at = b.records_at + b.record_offsets[c]
+            assert v2[at:at + len(raw)] == raw
+        else:
+            assert not b.stored[c] and b.table[c] == a.table[c] and b.tokens[c] == a.tokens[c]
+    assert oracle.decompress(v2).tobytes() == xb
+    assert oracle.decompress(v1).tobytes() == xb
+
+
+def test_v2_decoder_rejects_bad_stored_chunks():
+    x = np.frombuffer(bytes(range(64)), np.uint8)  # nothing repeats: all stored
+    good = bytearray(oracle.compress(x, Params(1, 16, 8, 3, 255), version=2).tobytes())
+    assert oracle.decompress_status(bytes(good)) == 0
+    b = bytearray(good); b[36] = 15; assert oracle.decompress_status(bytes(b)) == oracle.ECORRUPT
+    b = bytearray(good); b[4] = 1; assert oracle.decompress_status(bytes(b)) == oracle.ECORRUPT
+    b = bytearray(good); b[4] = 3; assert oracle.decompress_status(bytes(b)) == oracle.ECORRUPT
