@@ -15,9 +15,12 @@ are sampled with nvidia-smi during the timed region.  Under torchrun each
 rank compresses its own shard (independent data, weak scaling); there is no
 data-path collective.
 
-After the timed steps (not part of them) the line gets three more sections
-on the same GPU: `paper_matcher` -- the paper's own matcher (section 3.3.2)
-beside the exact one on 256 MiB of uint16 quantization codes; `batched` --
+After the timed steps (not part of them) the line gets more sections on
+the same GPU: `stream_version2` -- the same items as stream version 2
+(stored chunks); `paper_matcher` -- the paper's own matcher (section 3.3.2)
+beside the exact one on 256 MiB of uint16 quantization codes; `huffman` --
+the paper's use case (section 4.4), Huffman coding after LZSS, on the same
+codes; `batched` --
 10,000 uneven buffers (4 KiB-16 MiB, four
 kinds, about 20 GB) compressed and decompressed by one persistent launch
 under a CUDA graph vs one plain launch per buffer -- and `served` -- a
@@ -335,6 +338,8 @@ def run_gpu(args):
     torch.cuda.empty_cache()
     if args.paper_matcher:
         line["paper_matcher"] = _paper_matcher(torch, codec, args)
+    if args.huffman:
+        line["huffman"] = _huffman(torch, codec, args)
     if args.batched:
         line["batched"] = _batched(torch, codec, args)
     if args.served > 0:
@@ -369,6 +374,64 @@ def _paper_matcher(torch, codec, args, n_sym: int = 128 << 20):
                      "ratio": round(d.numel() / int(nb.item()), 4)}
         del buf
     del d
+    torch.cuda.empty_cache()
+    return out
+
+
+def _huffman(torch, codec, args, n_sym: int = 128 << 20, reps: int = 5):
+    """The paper's use case (section 4.4): Huffman coding after LZSS, on 256
+    MiB of uint16 quantization codes.  Ratios of Huffman alone, LZSS alone
+    and LZSS then Huffman; GB/s of the Huffman encoder (input bytes) and
+    decoder (output bytes), CUDA events over `reps` calls."""
+    from paper_2304_07342_gb300 import lz, synth
+    x = synth.quant_codes_laplace(n_sym, seed=args.seed)
+    d = torch.from_numpy(x.view(np.uint8)).cuda()
+    st = torch.cuda.current_stream()
+    n = d.numel()
+
+    def huff(src, nbytes):
+        cap = lz.lz_huff_bound(nbytes)
+        out = torch.empty(cap, dtype=torch.uint8, device="cuda")
+        nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+        lz.lz_huff_compress(codec.ctx, src.data_ptr(), nbytes, out.data_ptr(), cap, nb.data_ptr(),
+                            st.cuda_stream)
+        if codec.sync() != lz.LZ_OK:
+            raise RuntimeError("huffman compress failed on the device")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            lz.lz_huff_compress(codec.ctx, src.data_ptr(), nbytes, out.data_ptr(), cap,
+                                nb.data_ptr(), st.cuda_stream)
+        b.record(st)
+        torch.cuda.synchronize()
+        return out, int(nb.item()), a.elapsed_time(b) / reps
+
+    h1, h1_bytes, h1_ms = huff(d, n)
+    back = torch.empty_like(d)
+    nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+    lz.lz_huff_decompress(codec.ctx, h1.data_ptr(), h1_bytes, back.data_ptr(), n, nb.data_ptr(),
+                          st.cuda_stream)
+    if codec.sync() != lz.LZ_OK or not torch.equal(back, d):
+        raise RuntimeError("huffman round trip failed")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        lz.lz_huff_decompress(codec.ctx, h1.data_ptr(), h1_bytes, back.data_ptr(), n,
+                              nb.data_ptr(), st.cuda_stream)
+    b.record(st)
+    torch.cuda.synchronize()
+    dec_ms = a.elapsed_time(b) / reps
+    del h1, back
+    s1 = codec.compress_sync(d, lz.Params(2, 4096, 128, 3, 255))
+    h2, h2_bytes, h2_ms = huff(s1, s1.numel())
+    out = {"workload": f"uint16 quant codes, {n >> 20} MiB; LZSS S=2 C=4096 W=128 m=3 M=255",
+           "huffman_only": {"ratio": round(n / h1_bytes, 4),
+                            "compress_gbs": round(n / (h1_ms * 1e-3) / 1e9, 2),
+                            "decompress_gbs": round(n / (dec_ms * 1e-3) / 1e9, 2)},
+           "lzss_only": {"ratio": round(n / s1.numel(), 4)},
+           "lzss_then_huffman": {"ratio": round(n / h2_bytes, 4),
+                                 "huffman_gbs_on_stream": round(s1.numel() / (h2_ms * 1e-3) / 1e9, 2)}}
+    del d, s1, h2
     torch.cuda.empty_cache()
     return out
 
@@ -546,6 +609,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-version2", dest="version2", action="store_false",
                     help="skip the stream-version-2 (stored chunks) pass")
+    ap.add_argument("--no-huffman", dest="huffman", action="store_false",
+                    help="skip the LZSS-then-Huffman use case")
     ap.add_argument("--no-paper-matcher", dest="paper_matcher", action="store_false",
                     help="skip the exact-vs-paper matcher comparison")
     ap.add_argument("--no-batched", dest="batched", action="store_false",

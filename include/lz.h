@@ -15,8 +15,10 @@
  * when its length is >= m, else a literal.  Output is byte-identical to the
  * CPU definition for the same parameters.
  *
- * Stream layout "GLZ1" (all integers little-endian):
- *   header  32 B: "GLZ1", u8 version (1), u8 S, u8 offB, u8 m, u8 M,
+ * Stream layout "GLZ1" (all integers little-endian; version 2, written by
+ * lz_compress_ex on request, adds stored chunks and tail bytes, see
+ * lz_options):
+ *   header  32 B: "GLZ1", u8 version (1 or 2), u8 S, u8 offB, u8 m, u8 M,
  *           3 zero bytes, u32 chunk_bytes, u32 W, u32 n_chunks, u64 n_bytes
  *   table   n_chunks x {u32 n_tokens, u32 payload_bytes}
  *   index   ceil(n_chunks/64) x u64: offset of the record of chunk 64*j,
@@ -125,7 +127,17 @@ lz_status lz_compress(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
  * LZ_MATCH_EXACT and stream version 1, i.e. exactly lz_compress. */
 typedef struct lz_options {
   uint32_t match;   /* lz_match                                          */
-  uint32_t version; /* stream version written: 0 or 1 = GLZ1 version 1   */
+  uint32_t version; /* stream version written: 0 or 1 = version 1 above;
+                       2 = the same layout with version byte 2, in which
+                       (a) a chunk whose coded record (flag bytes +
+                       payload) would not be smaller than the chunk is
+                       stored as it is: table entry {0, chunk bytes},
+                       record = the chunk's bytes, no flags (a coded
+                       chunk has >= 1 token, so 0 marks it); and (b)
+                       n_bytes need not be a multiple of S: the last
+                       chunk's 1..S-1 bytes after its last whole symbol
+                       follow its tokens as they are, counted in its
+                       payload_bytes.  lz_decompress reads both.       */
 } lz_options;
 
 /* lz_compress with options (opt may be NULL: the defaults).
@@ -137,8 +149,9 @@ typedef struct lz_options {
  * symbols; the parse takes a pointer when the kept run has >= m symbols.
  * Positions without any match of >= m symbols are literals under both
  * matchers, and the stream header does not record the matcher.
- * LZ_ERR_INVALID_ARG for an unknown matcher or version; everything else as
- * for lz_compress. */
+ * LZ_ERR_INVALID_ARG for an unknown matcher or version, or for
+ * n_bytes % S != 0 in version 1; everything else as for lz_compress
+ * (lz_compressed_bound covers both versions, a tail included). */
 lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
                          const lz_params *p, const lz_options *opt, void *d_out,
                          uint64_t out_cap, uint64_t *d_out_bytes, lz_stream_t stream);
@@ -283,6 +296,56 @@ lz_status lz_stitch(lz_ctx *ctx, const void *d_shard, uint64_t shard_bytes,
  * error (LZ_OK if none).  When several errors occurred the most severe is
  * returned: INTERNAL, TIMEOUT, CORRUPT, then BUFFER_TOO_SMALL. */
 lz_status lz_sync(lz_ctx *ctx, lz_stream_t stream);
+
+/* ---- Huffman stage ----------------------------------------------------------
+ * In the paper's use case (section 4.4) gpuLZ runs before cuSZ's Huffman
+ * encoding.  The paper does not print that stage, so its definition here is
+ * this library's: a byte-alphabet prefix code, optimal among codes whose
+ * lengths do not exceed 12 bits (package-merge; ties: a leaf before a
+ * package of equal weight, leaves by (count, value)), with canonical codes
+ * (symbols in order of (length, value) take consecutive values).
+ *
+ * Stream "GHF1" (integers little-endian):
+ *   [0,16)    "GHF1", u32 block bytes (32768), u64 n_bytes
+ *   [16,272)  256 x u8: code length of each byte value (0 = absent)
+ *   table     n_blocks x u64: end of each block's bit string, in bytes from
+ *             the start of `bits`; block b spans [end[b-1], end[b])
+ *   subs      n_blocks x 32 x u32: bit offset, inside its block, of each of
+ *             its 32 sub-blocks of 1024 input bytes (sub-blocks past the end
+ *             of the input repeat the end offset)
+ *   bits      per block, a whole number of u32 words; bit i of a block is
+ *             bit 31 - (i % 32) of its word i / 32; codes most significant
+ *             bit first; padding bits 0.
+ * n_blocks = ceil(n_bytes / 32768); `bits` starts at 272 + 136 n_blocks. */
+
+/* Largest GHF1 stream for n_bytes of input (pure host). */
+uint64_t lz_huff_bound(uint64_t n_bytes);
+
+/* Huffman-code n_bytes at d_in (any alignment) into d_out (8-byte aligned,
+ * capacity out_cap) and store the stream size in *d_out_bytes (device
+ * uint64, 8-byte aligned).  Five launches (histogram, code book, sub-block
+ * sizes, block offsets, encode); no host synchronisation.  out_cap below
+ * the header and tables is LZ_ERR_BUFFER_TOO_SMALL at once; a stream that
+ * does not fit is reported by lz_sync (LZ_ERR_BUFFER_TOO_SMALL) with the
+ * size that was needed in *d_out_bytes.  lz_huff_bound(n_bytes) always
+ * suffices.  Uses the context's scratch, like lz_compress. */
+lz_status lz_huff_compress(lz_ctx *ctx, const void *d_in, uint64_t n_bytes, void *d_out,
+                           uint64_t out_cap, uint64_t *d_out_bytes, lz_stream_t stream);
+
+/* n_bytes of the GHF1 stream at d_in (reads its 16-byte header; synchronises
+ * `stream`).  LZ_ERR_CORRUPT for a bad header or a stream shorter than its
+ * tables. */
+lz_status lz_huff_decompressed_size(const void *d_in, uint64_t in_bytes, uint64_t *h_n,
+                                    lz_stream_t stream);
+
+/* Decode the GHF1 stream at d_in (8-byte aligned, in_bytes long) into d_out
+ * (capacity out_cap) and store n_bytes in *d_out_bytes.  One launch; the
+ * kernel reads the header and tables itself.  A bad header, code lengths
+ * that do not form a complete code, block ends or sub-block offsets that
+ * disagree with the bits, or a code not in the table are LZ_ERR_CORRUPT;
+ * out_cap < n_bytes is LZ_ERR_BUFFER_TOO_SMALL; both come from lz_sync. */
+lz_status lz_huff_decompress(lz_ctx *ctx, const void *d_in, uint64_t in_bytes, void *d_out,
+                             uint64_t out_cap, uint64_t *d_out_bytes, lz_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -16,7 +16,9 @@ computes, and which passage of the paper it follows, is documented in
   matching steps), a heuristic that never exceeds :func:`longest_match`;
 * :func:`parse_chunk` -- section 2.2 steps 1-6 inside one chunk (3.3.1),
   with either matcher;
-* :func:`compress` / :func:`decompress` -- the whole chunked stream.
+* :func:`compress` / :func:`decompress` -- the whole chunked stream;
+* :func:`huff_compress` / :func:`huff_decompress` -- the Huffman stage that
+  follows LZSS in section 4.4's use case (``huffref.h``).
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (brute force, closed forms, hand-worked fixtures, round trip).
@@ -31,7 +33,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "lzref.c")
+_SRCS = [os.path.join(_HERE, "lzref.c"), os.path.join(_HERE, "huffref.c")]
 _LIB_PATH = os.path.join(_HERE, "liblzref.so")
 
 OK, EINVAL, ESMALL, ECORRUPT = 0, 1, 2, 3
@@ -44,13 +46,15 @@ class OracleError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    """Compile ``lzref.c`` into ``liblzref.so`` next to it (gcc, -O2)."""
+    """Compile ``lzref.c`` and ``huffref.c`` into ``liblzref.so`` next to
+    them (gcc, -O2)."""
+    deps = _SRCS + [s[:-2] + ".h" for s in _SRCS]
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(d) for d in deps)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-Wextra",
-                           "-shared", "-fPIC", "-o", tmp, _SRC])
+                           "-shared", "-fPIC", "-o", tmp, *_SRCS])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -88,6 +92,18 @@ def _load():
         lib.lzref_compress_v.argtypes = [u8p, u64] + [u32] * 7 + [
             u8p, u64, u64p]
         lib.lzref_compress_v.restype = ctypes.c_int
+        lib.huffref_lengths.argtypes = [u64p, u32, u8p]
+        lib.huffref_lengths.restype = None
+        lib.huffref_codes.argtypes = [u8p, u32p]
+        lib.huffref_codes.restype = None
+        lib.huffref_bound.argtypes = [u64]
+        lib.huffref_bound.restype = u64
+        lib.huffref_compress.argtypes = [u8p, u64, u8p, u64, u64p]
+        lib.huffref_compress.restype = ctypes.c_int
+        lib.huffref_decompressed_size.argtypes = [u8p, u64, u64p]
+        lib.huffref_decompressed_size.restype = ctypes.c_int
+        lib.huffref_decompress.argtypes = [u8p, u64, u8p, u64, u64p]
+        lib.huffref_decompress.restype = ctypes.c_int
         lib.lzref_compress.argtypes = [u8p, u64] + [u32] * 5 + [u8p, u64,
                                                                 u64p]
         lib.lzref_compress.restype = ctypes.c_int
@@ -260,3 +276,62 @@ def select_params(sample, dtype_bytes: int, level: int = 3,
         raise OracleError(EINVAL, "select_params")
     size = compress(b, multi).size
     return single if ratio_below(b.size, size) else multi
+
+
+# --- Huffman stage after LZSS (section 4.4's use case), huffref.c ----------------
+
+HUFF_MAX_LEN, HUFF_BLOCK, HUFF_SUB = 12, 32768, 1024
+
+
+def huff_lengths(hist, max_len: int = HUFF_MAX_LEN) -> np.ndarray:
+    """Code lengths (0 = absent) of the optimal prefix code with lengths <=
+    max_len for 256 counts (package-merge, tie rules in huffref.c)."""
+    h = np.ascontiguousarray(hist, dtype=np.uint64)
+    assert h.size == 256
+    out = np.zeros(256, np.uint8)
+    _load().huffref_lengths(h.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                            max_len, _ptr(out))
+    return out
+
+
+def huff_codes(lengths) -> np.ndarray:
+    """Canonical code of each byte value for the given lengths."""
+    ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+    out = np.zeros(256, np.uint32)
+    _load().huffref_codes(_ptr(ln), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    return out
+
+
+def huff_bound(n: int) -> int:
+    return int(_load().huffref_bound(n))
+
+
+def huff_compress(data) -> np.ndarray:
+    b = _bytes(data)
+    cap = int(_load().huffref_bound(b.size))
+    out = np.empty(cap, np.uint8)
+    nb = ctypes.c_uint64()
+    rc = _load().huffref_compress(_ptr(b), b.size, _ptr(out), cap, ctypes.byref(nb))
+    if rc != OK:
+        raise OracleError(rc, "huff_compress")
+    return out[: nb.value].copy()
+
+
+def huff_decompress_status(stream):
+    """(return code, bytes) of decoding a GHF1 stream."""
+    b = _bytes(stream)
+    n = ctypes.c_uint64()
+    rc = _load().huffref_decompressed_size(_ptr(b), b.size, ctypes.byref(n))
+    if rc != OK:
+        return rc, None
+    out = np.empty(max(n.value, 1), np.uint8)
+    nb = ctypes.c_uint64()
+    rc = _load().huffref_decompress(_ptr(b), b.size, _ptr(out), n.value, ctypes.byref(nb))
+    return rc, (out[: n.value].copy() if rc == OK else None)
+
+
+def huff_decompress(stream) -> np.ndarray:
+    rc, out = huff_decompress_status(stream)
+    if rc != OK:
+        raise OracleError(rc, "huff_decompress")
+    return out

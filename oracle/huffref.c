@@ -148,7 +148,7 @@ static uint64_t h_div_up(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 uint64_t huffref_bound(uint64_t n) {
   uint64_t nb = h_div_up(n, HUFFREF_BLOCK);
   /* every byte at most HUFFREF_MAX_LEN bits, each block padded to words */
-  return H_HEADER + H_LENGTHS + nb * 4u + nb * H_SUBS * 4u +
+  return H_HEADER + H_LENGTHS + nb * 8u + nb * H_SUBS * 4u +
          h_div_up(n * HUFFREF_MAX_LEN, 32) * 4u + nb * 4u;
 }
 
@@ -170,7 +170,7 @@ int huffref_compress(const uint8_t *in, uint64_t n, uint8_t *out,
   uint64_t nb = h_div_up(n, HUFFREF_BLOCK);
   if (nb > 0xFFFFFFFFull) return H_EINVAL;
   uint64_t table_at = H_HEADER + H_LENGTHS;
-  uint64_t subs_at = table_at + 4u * nb;
+  uint64_t subs_at = table_at + 8u * nb;
   uint64_t bits_at = subs_at + 4u * H_SUBS * nb;
   if (cap < bits_at) return H_ESMALL;
   memset(out, 0, (size_t)bits_at);
@@ -206,8 +206,8 @@ int huffref_compress(const uint8_t *in, uint64_t n, uint8_t *out,
         for (uint32_t j = 0; j < l; ++j) h_put_bit(blk, bit++, (c >> (l - 1 - j)) & 1u);
       }
     }
-    h_put_u32(out + table_at + 4u * b, (uint32_t)bytes);
     pos += bytes;
+    h_put_u64(out + table_at + 8u * b, pos - bits_at);
   }
   *out_bytes = pos;
   return H_OK;
@@ -250,12 +250,14 @@ int huffref_decompress(const uint8_t *in, uint64_t in_bytes, uint8_t *out,
   huffref_codes(len, code);
   uint64_t nb = h_div_up(n, HUFFREF_BLOCK);
   uint64_t table_at = H_HEADER + H_LENGTHS;
-  uint64_t subs_at = table_at + 4u * nb;
+  uint64_t subs_at = table_at + 8u * nb;
   uint64_t bits_at = subs_at + 4u * H_SUBS * nb;
   if (in_bytes < bits_at) return H_ECORRUPT;
   uint64_t pos = bits_at;
   for (uint64_t b = 0; b < nb; ++b) {
-    uint64_t bytes = h_get_u32(in + table_at + 4u * b);
+    uint64_t end = h_get_u64(in + table_at + 8u * b);
+    if (end < pos - bits_at) return H_ECORRUPT;
+    uint64_t bytes = end - (pos - bits_at);
     if (bytes % 4 || pos + bytes > in_bytes) return H_ECORRUPT;
     const uint8_t *blk = in + pos;
     uint64_t lo = b * HUFFREF_BLOCK;

@@ -18,7 +18,9 @@
  *   - stream "GHF1" (integers little-endian):
  *       [0,16)    "GHF1", u32 block bytes (HUFFREF_BLOCK), u64 n_bytes
  *       [16,272)  256 x u8 code length of each byte value
- *       table     n_blocks x u32: bytes of each block's bit string
+ *       table     n_blocks x u64: end of each block's bit string, in bytes
+ *                 from the start of `bits` (block b spans [end[b-1], end[b]),
+ *                 end[-1] = 0)
  *       subs      n_blocks x 32 x u32: bit offset, inside its block's bit
  *                 string, of each of the block's 32 sub-blocks of
  *                 HUFFREF_SUB input bytes (offset 0 first; sub-blocks past

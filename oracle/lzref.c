@@ -56,7 +56,7 @@ uint64_t lzref_bound(uint64_t n, uint32_t S, uint32_t C, uint32_t W,
   uint32_t offB = ref_off_bytes(W);
   for (uint64_t c = 0; c < nc; ++c) {
     uint64_t bytes = (c + 1 < nc) ? C : n - c * (uint64_t)C;
-    total += ref_record_bound(bytes / S, S, offB, m);
+    total += ref_record_bound(bytes / S, S, offB, m) + bytes % S;
   }
   return total;
 }
@@ -217,7 +217,7 @@ int lzref_compress_v(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
   if (lzref_check_params(S, C, W, m, M) != REF_OK) return REF_EINVAL;
   if (mode != LZREF_MATCH_EXACT && mode != LZREF_MATCH_PAPER) return REF_EINVAL;
   if (version != 1 && version != 2) return REF_EINVAL;
-  if (n % S != 0) return REF_EINVAL;
+  if (version == 1 && n % S != 0) return REF_EINVAL;
   uint64_t nc = ref_div_up(n, C);
   if (nc > 0xFFFFFFFFull) return REF_EINVAL;
   uint32_t offB = ref_off_bytes(W);
@@ -265,6 +265,10 @@ int lzref_compress_v(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
     uint64_t payload = 0;
     for (uint32_t t = 0; t < ntok; ++t)
       payload += tok_off[t] ? 1u + offB : S;
+    /* version 2: the 1..S-1 bytes past the last whole symbol (last chunk
+     * only) follow the tokens, as they are */
+    uint32_t tail = (uint32_t)(bytes - (uint64_t)k * S);
+    payload += tail;
 
     /* version 2: a chunk whose coded record would not be smaller than its
      * bytes is stored as they are, marked by a token count of 0 */
@@ -303,6 +307,7 @@ int lzref_compress_v(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
       }
       p += tok_len[t];
     }
+    memcpy(pay, chunk + (size_t)k * S, tail);
     pos += flag_bytes + payload;
   }
   free(tok_len);
@@ -330,7 +335,7 @@ static int ref_read_header(const uint8_t *in, uint64_t in_bytes,
   *n = ref_get_u64(in + 24);
   if (lzref_check_params(*S, *C, *W, *m, *M) != REF_OK) return REF_ECORRUPT;
   if (*offB != ref_off_bytes(*W)) return REF_ECORRUPT;
-  if (*n % *S != 0) return REF_ECORRUPT;
+  if (in[4] == 1 && *n % *S != 0) return REF_ECORRUPT; /* tails: version 2 */
   if (*nc != ref_div_up(*n, *C)) return REF_ECORRUPT;
   return REF_OK;
 }
@@ -405,7 +410,9 @@ int lzref_decompress(const uint8_t *in, uint64_t in_bytes, uint8_t *out,
         p += 1;
       }
     }
-    if (p != k || pay != pay_end) return REF_ECORRUPT;
+    uint32_t tail = (uint32_t)(bytes - (uint64_t)k * S);
+    if (p != k || pay + tail != pay_end) return REF_ECORRUPT;
+    memcpy(dst + (size_t)k * S, pay, tail);
     pos += flag_bytes + payload;
   }
   *out_bytes = n;

@@ -42,7 +42,8 @@ extern "C" {
 int lzref_check_params(uint32_t S, uint32_t C, uint32_t W, uint32_t m,
                        uint32_t M);
 
-/* Largest stream compress can produce for n bytes; 0 for invalid params. */
+/* Largest stream compress can produce for n bytes (any version; a tail of
+ * n % S bytes adds itself); 0 for invalid params. */
 uint64_t lzref_bound(uint64_t n, uint32_t S, uint32_t C, uint32_t W,
                      uint32_t m, uint32_t M);
 
@@ -93,7 +94,10 @@ int lzref_compress_mode(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
  *      (flag bytes + payload) would be at least as large as the chunk
  *      itself is stored instead: table entry {0, chunk bytes}, record =
  *      the chunk's bytes (no flags).  A coded chunk always has >= 1 token,
- *      so a token count of 0 marks a stored chunk unambiguously.
+ *      so a token count of 0 marks a stored chunk unambiguously.  n need
+ *      not be a multiple of S: the last chunk's 1..S-1 bytes past its last
+ *      whole symbol follow its payload as they are (counted in
+ *      payload_bytes), and a chunk with no whole symbol is stored.
  * The decoder reads both versions. */
 int lzref_compress_v(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
                      uint32_t W, uint32_t m, uint32_t M, uint32_t mode,

@@ -966,6 +966,15 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
     payload = W.pay;
   }
   if (!sane && lane == 0) atomicOr(A.err, kErrInternal);
+  // stream version 2, last chunk: the 1..S-1 bytes after the last whole
+  // symbol follow the tokens as they are (in the staged chunk they already
+  // follow the k symbols)
+  const uint32_t tail = bytes - k * S;
+  if (tail) {
+    if (payload != W.inb && lane < tail) W.pay[pb + lane] = W.inb[k * S + lane];
+    __syncwarp();
+    pb += tail;
+  }
   uint32_t fb = (ntok + 7) / 8;
   if (B.version == 2 && fb + pb >= bytes) {
     // stream version 2: a record that would not be smaller than the chunk is

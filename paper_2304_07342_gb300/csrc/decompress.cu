@@ -55,7 +55,7 @@ __device__ __forceinline__ bool read_header(const uint8_t *in, Header &h) {
   ok = ok && h.W >= 1 && h.W <= kMaxWindow;
   ok = ok && h.m >= 1 && h.m <= h.M && h.M <= 255;
   ok = ok && h.offB == (h.W <= 256 ? 1u : 2u);
-  ok = ok && h.n % h.S == 0;
+  ok = ok && (h.version == 2 || h.n % h.S == 0);  // version 2 allows a tail
   ok = ok && static_cast<uint64_t>(h.nc) == (h.n + h.C - 1) / h.C;
   return ok;
 }
@@ -174,14 +174,15 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
   const uint64_t fb = (static_cast<uint64_t>(ntok) + 7) / 8;
   const uint64_t rec_at = records_at + idxv + part;
   const uint64_t chunk_at = static_cast<uint64_t>(c) * h.C;
-  const uint32_t k = static_cast<uint32_t>(
-      ((c + 1 < h.nc) ? h.C : h.n - chunk_at) / h.S);
+  const uint32_t bytes_c = static_cast<uint32_t>((c + 1 < h.nc) ? h.C : h.n - chunk_at);
+  const uint32_t k = bytes_c / h.S;
+  const uint32_t tail = bytes_c - k * h.S;  // version 2, last chunk: bytes after the last symbol
   // version 2: a token count of 0 marks a stored chunk (its bytes as they are)
   const bool stored = h.version == 2 && ntok == 0;
   bad = bad || idxv > A.in_bytes || rec_at + fb + pay > A.in_bytes ||
-        rec_at + fb + pay < rec_at || ntok > k || (ntok == 0 && k > 0 && !stored) ||
-        (stored && static_cast<uint64_t>(pay) != static_cast<uint64_t>(k) * h.S) ||
-        fb + pay > record_bound(k, h);
+        rec_at + fb + pay < rec_at || ntok > k || (ntok == 0 && !stored) ||
+        (stored && pay != bytes_c) || (!stored && pay < tail) ||
+        fb + pay > record_bound(k, h) + tail;
   if (bad) {
     if (lane == 0) atomicOr(A.err, kErrCorrupt);
     return true;
@@ -212,7 +213,7 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
     uint32_t any = 0;
     for (uint32_t i = lane; i < fb; i += 32) any |= flags[i];
     if (!__any_sync(kFull, any != 0)) {
-      if (ntok != k || static_cast<uint64_t>(pay) != static_cast<uint64_t>(k) * S) {
+      if (ntok != k || pay != bytes_c) {
         if (lane == 0) atomicOr(A.err, kErrCorrupt);
         return true;
       }
@@ -225,6 +226,7 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
 
   uint32_t pos = 0;       // symbols produced
   uint64_t pay_used = 0;  // payload bytes consumed
+  const uint32_t pay_tok = pay - tail;  // the tokens' payload; the tail follows it
   for (uint32_t tb = 0; tb < ntok; tb += 32) {
     const uint32_t t = tb + lane;
     const bool valid = t < ntok;
@@ -235,7 +237,7 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
     const uint32_t nlb = __popc(vm & ~mm & lt);
     const uint64_t my_off = pay_used + S * nlb + tsz * nmb;
     const uint32_t my_sz = ism ? tsz : (valid ? S : 0u);
-    bool tbad = valid && my_off + my_sz > pay;
+    bool tbad = valid && my_off + my_sz > pay_tok;
     uint32_t len = valid ? 1u : 0u, off = 0, val = 0;
     if (valid && !tbad) {
       if (ism) {
@@ -307,8 +309,10 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
     pos = end;
     pay_used += S * __popc(vm & ~mm) + tsz * __popc(mm);
   }
-  if (pos != k || pay_used != pay) {
+  if (pos != k || pay_used != pay_tok) {
     if (lane == 0) atomicOr(A.err, kErrCorrupt);
+  } else if (lane < tail) {
+    dst[static_cast<uint64_t>(k) * S + lane] = payload[pay_tok + lane];
   }
   return true;
 }

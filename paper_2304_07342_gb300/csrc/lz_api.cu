@@ -26,6 +26,13 @@ cudaError_t launch_compress_batch(const CompressArgs &A, const BufDesc *empties,
                                   cudaStream_t stream);
 cudaError_t launch_decompress_batch(DecompressBatchArgs B, int block, cudaStream_t stream);
 cudaError_t launch_stitch(const StitchArgs &A, int sms, cudaStream_t stream);
+cudaError_t launch_huff_compress(const uint8_t *in, uint64_t n, uint8_t *out, uint64_t out_cap,
+                                 unsigned long long *out_bytes, unsigned long long *hist,
+                                 uint32_t *book, uint32_t *err, int sms, cudaStream_t st);
+cudaError_t launch_huff_decompress(const uint8_t *in, uint64_t in_bytes, uint8_t *out,
+                                   uint64_t out_cap, unsigned long long *out_bytes,
+                                   uint32_t *err, int sms, cudaStream_t st);
+uint64_t huff_layout_bits_at(uint64_t n);
 
 // Gather the 32-byte headers of n streams into one device array.
 __global__ void gather_headers(const uint8_t *const *ins, const uint64_t *in_bytes,
@@ -38,12 +45,12 @@ __global__ void gather_headers(const uint8_t *const *ins, const uint64_t *in_byt
 }
 
 // Empty input: the stream is the header alone (n_chunks = 0, n_bytes = 0).
-__global__ void header_kernel(uint8_t *out, uint32_t S, uint32_t offB,
+__global__ void header_kernel(uint8_t *out, uint32_t version, uint32_t S, uint32_t offB,
                               uint32_t m, uint32_t M, uint32_t C, uint32_t W,
                               unsigned long long *out_bytes) {
   const uint32_t i = threadIdx.x;
   if (i >= kHeaderBytes) return;
-  const uint8_t fixed[9] = {'G', 'L', 'Z', '1', 1,
+  const uint8_t fixed[9] = {'G', 'L', 'Z', '1', static_cast<uint8_t>(version),
                             static_cast<uint8_t>(S), static_cast<uint8_t>(offB),
                             static_cast<uint8_t>(m), static_cast<uint8_t>(M)};
   uint8_t b = 0;
@@ -54,11 +61,11 @@ __global__ void header_kernel(uint8_t *out, uint32_t S, uint32_t offB,
   if (i == 0) *out_bytes = kHeaderBytes;
 }
 
-static cudaError_t launch_header(uint8_t *out, uint32_t S, uint32_t offB,
+static cudaError_t launch_header(uint8_t *out, uint32_t version, uint32_t S, uint32_t offB,
                                  uint32_t m, uint32_t M, uint32_t C, uint32_t W,
                                  unsigned long long *out_bytes,
                                  cudaStream_t stream) {
-  header_kernel<<<1, 32, 0, stream>>>(out, S, offB, m, M, C, W, out_bytes);
+  header_kernel<<<1, 32, 0, stream>>>(out, version, S, offB, m, M, C, W, out_bytes);
   return cudaGetLastError();
 }
 }  // namespace glz
@@ -190,7 +197,8 @@ uint64_t lz_compressed_bound(uint64_t n_bytes, const lz_params *p) {
                    8ull * div_up(nc, glz::kIndexStride);
   if (nc == 0) return total;
   total += (nc - 1) * record_bound(C / S, S, offB, p->min_match);
-  total += record_bound((n_bytes - (nc - 1) * C) / S, S, offB, p->min_match);
+  const uint64_t last = n_bytes - (nc - 1) * C;
+  total += record_bound(last / S, S, offB, p->min_match) + last % S;  // a tail adds itself
   return total;
 }
 
@@ -257,7 +265,7 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
   if (n_bytes > 0 && !d_in) return LZ_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(d_out_bytes) % 8 != 0) return LZ_ERR_INVALID_ARG;
   const uint32_t S = p->symbol_bytes, C = p->chunk_bytes;
-  if (n_bytes % S != 0) return LZ_ERR_INVALID_ARG;
+  if (version == 1 && n_bytes % S != 0) return LZ_ERR_INVALID_ARG;  // tails: version 2
   const uint64_t nc = div_up(n_bytes, C);
   if (nc > 0xFFFFFFFFull) return LZ_ERR_INVALID_ARG;
   const uint64_t records_at = glz::kHeaderBytes + glz::kTableEntry * nc +
@@ -269,7 +277,7 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
   const uint32_t offB = off_bytes(p->window);
   auto *out_bytes = reinterpret_cast<unsigned long long *>(d_out_bytes);
   if (nc == 0)
-    return cuda_status(glz::launch_header(static_cast<uint8_t *>(d_out), S, offB,
+    return cuda_status(glz::launch_header(static_cast<uint8_t *>(d_out), version, S, offB,
                                           p->min_match, p->max_match, C,
                                           p->window, out_bytes, st));
 
@@ -358,7 +366,7 @@ lz_status lz_decompressed_size(const void *d_in, uint64_t in_bytes,
   for (int i = 0; i < 8; ++i) n |= static_cast<uint64_t>(h[24 + i]) << (8 * i);
   lz_params p{h[5], u32(12), u32(16), h[7], h[8]};
   if (std::memcmp(h, "GLZ1", 4) != 0 || (h[4] != 1 && h[4] != 2) || h[9] || h[10] || h[11] ||
-      !params_ok(&p) || h[6] != off_bytes(p.window) || n % p.symbol_bytes != 0 ||
+      !params_ok(&p) || h[6] != off_bytes(p.window) || (h[4] == 1 && n % p.symbol_bytes != 0) ||
       u32(20) != div_up(n, p.chunk_bytes))
     return LZ_ERR_CORRUPT;
   *h_n = n;
@@ -535,7 +543,7 @@ extern "C" lz_status lz_compress_noalloc(const void *d_in, uint64_t n_bytes,
   const uint32_t offB = off_bytes(p->window);
   auto *out_bytes = reinterpret_cast<unsigned long long *>(d_out_bytes);
   if (nc == 0)
-    return cuda_status(glz::launch_header(static_cast<uint8_t *>(d_out), S, offB,
+    return cuda_status(glz::launch_header(static_cast<uint8_t *>(d_out), 1u, S, offB,
                                           p->min_match, p->max_match, C, p->window,
                                           out_bytes, st));
   const glz::CompressSmem sm = compress_layout(p);
@@ -824,7 +832,7 @@ lz_status batch_create_decompress(lz_ctx *ctx, const lz_batch_item *items, uint3
     const uint64_t nn = header_u(h, 24, 8);
     const uint64_t nc = header_u(h, 20, 4);
     if (std::memcmp(h, "GLZ1", 4) != 0 || (h[4] != 1 && h[4] != 2) || h[9] || h[10] || h[11] ||
-        !params_ok(&p) || h[6] != off_bytes(p.window) || nn % p.symbol_bytes != 0 ||
+        !params_ok(&p) || h[6] != off_bytes(p.window) || (h[4] == 1 && nn % p.symbol_bytes != 0) ||
         nc != div_up(nn, p.chunk_bytes))
       return LZ_ERR_CORRUPT;
     if (items[i].out_cap < nn || (nn > 0 && !items[i].d_out)) return LZ_ERR_BUFFER_TOO_SMALL;
@@ -1043,6 +1051,67 @@ lz_status lz_select_params(lz_ctx *ctx, const void *d_sample, uint64_t sample_by
   // ratio n / size below 3/2, in integers
   *out = (2 * sample_bytes < 3 * size) ? single : multi;
   return LZ_OK;
+}
+
+// ---- Huffman stage (the paper's use case: Huffman coding after LZSS) ----------
+
+uint64_t lz_huff_bound(uint64_t n_bytes) {
+  const uint64_t nb = div_up(n_bytes, 32768);
+  return glz::huff_layout_bits_at(n_bytes) + div_up(n_bytes * 12, 32) * 4 + 4 * nb;
+}
+
+lz_status lz_huff_compress(lz_ctx *ctx, const void *d_in, uint64_t n_bytes, void *d_out,
+                           uint64_t out_cap, uint64_t *d_out_bytes, lz_stream_t stream) {
+  if (!ctx || !d_out || !d_out_bytes) return LZ_ERR_INVALID_ARG;
+  if (n_bytes > 0 && !d_in) return LZ_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(d_out) % 8 || reinterpret_cast<uintptr_t>(d_out_bytes) % 8)
+    return LZ_ERR_INVALID_ARG;
+  if (n_bytes > (1ull << 44)) return LZ_ERR_INVALID_ARG;
+  if (out_cap < glz::huff_layout_bits_at(n_bytes)) return LZ_ERR_BUFFER_TOO_SMALL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
+  lz_status s = reserve_scratch(ctx, 4096);
+  if (s != LZ_OK) return s;
+  auto *hist = static_cast<unsigned long long *>(ctx->scratch);
+  auto *book = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(ctx->scratch) + 2048);
+  return cuda_status(glz::launch_huff_compress(
+      static_cast<const uint8_t *>(d_in), n_bytes, static_cast<uint8_t *>(d_out), out_cap,
+      reinterpret_cast<unsigned long long *>(d_out_bytes), hist, book, ctx->d_err, ctx->sms,
+      reinterpret_cast<cudaStream_t>(stream)));
+}
+
+lz_status lz_huff_decompressed_size(const void *d_in, uint64_t in_bytes, uint64_t *h_n,
+                                    lz_stream_t stream) {
+  if (!d_in || !h_n) return LZ_ERR_INVALID_ARG;
+  if (in_bytes < 272) return LZ_ERR_CORRUPT;
+  uint8_t h[16];
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(h, d_in, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return LZ_ERR_CUDA;
+  uint64_t n = 0;
+  for (int i = 0; i < 8; ++i) n |= static_cast<uint64_t>(h[8 + i]) << (8 * i);
+  const uint8_t blk[4] = {0x00, 0x80, 0x00, 0x00};  // 32768, little-endian
+  if (std::memcmp(h, "GHF1", 4) != 0 || std::memcmp(h + 4, blk, 4) != 0 ||
+      n > (1ull << 44) || glz::huff_layout_bits_at(n) > in_bytes)
+    return LZ_ERR_CORRUPT;
+  *h_n = n;
+  return LZ_OK;
+}
+
+lz_status lz_huff_decompress(lz_ctx *ctx, const void *d_in, uint64_t in_bytes, void *d_out,
+                             uint64_t out_cap, uint64_t *d_out_bytes, lz_stream_t stream) {
+  if (!ctx || !d_in || !d_out_bytes) return LZ_ERR_INVALID_ARG;
+  if (out_cap > 0 && !d_out) return LZ_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(d_in) % 8 || reinterpret_cast<uintptr_t>(d_out_bytes) % 8)
+    return LZ_ERR_INVALID_ARG;
+  if (in_bytes < 272) return LZ_ERR_CORRUPT;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
+  return cuda_status(glz::launch_huff_decompress(
+      static_cast<const uint8_t *>(d_in), in_bytes, static_cast<uint8_t *>(d_out), out_cap,
+      reinterpret_cast<unsigned long long *>(d_out_bytes), ctx->d_err, ctx->sms,
+      reinterpret_cast<cudaStream_t>(stream)));
 }
 
 }  // extern "C"

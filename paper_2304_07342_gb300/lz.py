@@ -36,7 +36,8 @@ EXPORTS = ("lz_create", "lz_destroy", "lz_status_string", "lz_check_params",
            "lz_compressed_bound", "lz_compress", "lz_compress_ex", "lz_decompressed_size",
            "lz_decompress", "lz_sync", "lz_compress_noalloc", "lz_batch_create",
            "lz_batch_run", "lz_batch_destroy", "lz_autotune", "lz_stitch",
-           "lz_select_params")
+           "lz_select_params", "lz_huff_bound", "lz_huff_compress",
+           "lz_huff_decompressed_size", "lz_huff_decompress")
 
 
 class LzError(RuntimeError):
@@ -122,6 +123,14 @@ def load(path: str = LIB_PATH):
     u32 = ctypes.c_uint32
     lib.lz_select_params.argtypes = [vp, vp, u64, u32, u32, u32, pp, vp]
     lib.lz_select_params.restype = i32
+    lib.lz_huff_bound.argtypes = [u64]
+    lib.lz_huff_bound.restype = u64
+    lib.lz_huff_compress.argtypes = [vp, vp, u64, vp, u64, vp, vp]
+    lib.lz_huff_compress.restype = i32
+    lib.lz_huff_decompressed_size.argtypes = [vp, u64, ctypes.POINTER(u64), vp]
+    lib.lz_huff_decompressed_size.restype = i32
+    lib.lz_huff_decompress.argtypes = [vp, vp, u64, vp, u64, vp, vp]
+    lib.lz_huff_decompress.restype = i32
     lib.lz_stitch.argtypes = [vp, vp, u64, u64, u64, u64, u64, u64, vp, u64, vp]
     lib.lz_stitch.restype = i32
     _lib = lib
@@ -235,6 +244,29 @@ def lz_select_params(ctx: int, d_sample: int, sample_bytes: int, dtype_bytes: in
     _check(load().lz_select_params(ctx, d_sample, sample_bytes, dtype_bytes, level, chunk_bytes,
                                    ctypes.byref(out), stream), "lz_select_params")
     return Params(out.symbol_bytes, out.chunk_bytes, out.window, out.min_match, out.max_match)
+
+
+def lz_huff_bound(n_bytes: int) -> int:
+    return int(load().lz_huff_bound(n_bytes))
+
+
+def lz_huff_compress(ctx: int, d_in: int, n_bytes: int, d_out: int, out_cap: int,
+                     d_out_bytes: int, stream: int = 0) -> None:
+    _check(load().lz_huff_compress(ctx, d_in, n_bytes, d_out, out_cap, d_out_bytes, stream),
+           "lz_huff_compress")
+
+
+def lz_huff_decompressed_size(d_in: int, in_bytes: int, stream: int = 0) -> int:
+    n = ctypes.c_uint64()
+    _check(load().lz_huff_decompressed_size(d_in, in_bytes, ctypes.byref(n), stream),
+           "lz_huff_decompressed_size")
+    return n.value
+
+
+def lz_huff_decompress(ctx: int, d_in: int, in_bytes: int, d_out: int, out_cap: int,
+                       d_out_bytes: int, stream: int = 0) -> None:
+    _check(load().lz_huff_decompress(ctx, d_in, in_bytes, d_out, out_cap, d_out_bytes, stream),
+           "lz_huff_decompress")
 
 
 def lz_sync(ctx: int, stream: int = 0) -> int:

@@ -76,7 +76,8 @@ def read(buf: bytes) -> Stream:
             else:
                 toks.append((1, 0))
                 q += S
-        assert q == pay, "payload size mismatch"
+        tail = min(C, n - c * C) % S if ver == 2 else 0  # version 2: bytes after the last symbol
+        assert q + tail == pay, "payload size mismatch"
         # padding bits of the last flag byte are zero
         if ntok % 8:
             assert flags[-1] >> (ntok % 8) == 0, "nonzero pad bits"

@@ -79,3 +79,8 @@ def test_product_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "lzref" not in text, f
+
+
+def test_huff_bound_matches_oracle(lib):
+    for n in (0, 1, 1023, 32768, 32769, 10**6, 1 << 30):
+        assert lz.lz_huff_bound(n) == oracle.huff_bound(n)

@@ -104,3 +104,24 @@ def test_v2_unknown_version_rejected(codec):
         lz.lz_compress_ex(codec.ctx, d.data_ptr(), 64, lz.Params(1, 64, 8, 2, 255),
                           out.data_ptr(), out.numel(), nb.data_ptr(),
                           torch.cuda.current_stream().cuda_stream, version=3)
+
+
+@pytest.mark.parametrize("S", [2, 4])
+@pytest.mark.parametrize("kind", ["alpha3", "quant", "random", "const"])
+def test_v2_tail_bytes(codec, S, kind):
+    """n % S != 0 (version 2): the bytes after the last whole symbol follow the
+    last chunk's payload; byte-identical to the oracle, round trip exact,
+    and version 1 still rejects such n."""
+    P = Params(S, 4096, 128, 2 if S == 4 else 3, 255)
+    base = make_input(kind, 3 * 4096 // S + 100, S, seed=S + 17).view(np.uint8)
+    for cut in (1, S - 1, 4096 + 1, 3 * 4096 + 3):
+        if cut % S == 0:
+            continue
+        x = np.ascontiguousarray(base[:cut])
+        ref = oracle.compress(x, P, version=2)
+        d = G.to_dev(x)
+        got = codec.compress_sync(d, lz.Params(*P.tuple()), version=2).cpu().numpy()
+        assert np.array_equal(got, ref), (cut, G.first_difference(got, ref))
+        assert np.array_equal(G.gpu_decompress(codec, got), x)
+        with pytest.raises(lz.LzError):
+            codec.compress(d, lz.Params(*P.tuple()))

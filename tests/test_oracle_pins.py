@@ -563,3 +563,31 @@ def test_v2_decoder_rejects_bad_stored_chunks():
     b = bytearray(good); b[36] = 15; assert oracle.decompress_status(bytes(b)) == oracle.ECORRUPT
     b = bytearray(good); b[4] = 1; assert oracle.decompress_status(bytes(b)) == oracle.ECORRUPT
     b = bytearray(good); b[4] = 3; assert oracle.decompress_status(bytes(b)) == oracle.ECORRUPT
+
+
+@pytest.mark.parametrize("S", [2, 4])
+def test_v2_tail_bytes(S):
+    """Version 2 takes n % S != 0: the last chunk's bytes after its last whole
+    symbol follow its payload as they are (version 1 rejects such n)."""
+    rng = np.random.default_rng(S)
+    for n in (1, S - 1, S + 1, 16 + 1, 16 * 3 + S + 1, 4096 * 2 + 3):
+        if n % S == 0:
+            continue
+        x = np.repeat(rng.integers(0, 4, n), 2)[:n].astype(np.uint8)
+        P = Params(S, 16 if n < 1000 else 4096, 8, 2 if S == 2 else 1, 255)
+        with pytest.raises(oracle.OracleError):
+            oracle.compress(x, P)
+        s = oracle.compress(x, P, version=2)
+        assert oracle.decompress(s).tobytes() == x.tobytes()
+        assert s.size <= oracle.bound(n, P)
+        st = glz1_reader.read(s.tobytes())
+        last = n - (st.n_chunks - 1) * P.C
+        k, tail = last // S, last % S
+        at = st.records_at + st.record_offsets[-1]
+        if st.stored[-1]:
+            assert s.tobytes()[at:at + last] == x.tobytes()[n - last:]
+        else:
+            ntok, pay = st.table[-1]
+            rec = s.tobytes()[at + (ntok + 7) // 8: at + (ntok + 7) // 8 + pay]
+            assert rec[-tail:] == x.tobytes()[n - tail:]
+            assert sum(l for l, _ in st.tokens[-1]) == k
