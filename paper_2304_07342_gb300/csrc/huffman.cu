@@ -443,7 +443,8 @@ __global__ void __launch_bounds__(256) huff_decode_kernel(const uint8_t *in, uin
     uint64_t lo, hi;
     sub_range(b, lane, h.n, lo, hi);
     const uint32_t o = bad ? 0 : subs[b * kHufSubs + lane];
-    const uint32_t o_next = lane < 31 ? __shfl_down_sync(kFull, o, 1) : 0u;
+    const uint32_t o_down = __shfl_down_sync(kFull, o, 1);  // every lane takes part
+    const uint32_t o_next = lane < 31 ? o_down : 0u;
     bad = bad || o > nbits || (lane == 0 && o != 0);
     if (__any_sync(kFull, bad)) {
       if (lane == 0) atomicOr(err, kErrCorrupt);
