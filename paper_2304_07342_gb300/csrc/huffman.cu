@@ -224,6 +224,31 @@ __device__ __forceinline__ void sub_range(uint64_t b, uint32_t lane, uint64_t n,
   if (lo > n) lo = n;
 }
 
+// The 32 bytes of sub-block s of block b that lane `lane` handles, as eight
+// little-endian words (zero past hi); 16-byte loads when `in` is aligned.
+__device__ __forceinline__ void lane_bytes(const uint8_t *in, uint64_t at, uint64_t hi,
+                                           bool in16, uint32_t (&w)[8]) {
+  if (in16 && at + 32 <= hi) {
+    const uint4 a = *reinterpret_cast<const uint4 *>(in + at);
+    const uint4 c = *reinterpret_cast<const uint4 *>(in + at + 16);
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    w[4] = c.x; w[5] = c.y; w[6] = c.z; w[7] = c.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      uint32_t v = 0;
+      for (int k = 0; k < 4; ++k) {
+        const uint64_t idx = at + 4 * q + k;
+        if (idx < hi) v |= static_cast<uint32_t>(in[idx]) << (8 * k);
+      }
+      w[q] = v;
+    }
+  }
+}
+
+// Code bits of each sub-block and their offsets inside the block.  One
+// warp per block; for each sub-block the lanes read 32 consecutive bytes
+// each (coalesced) and the warp sums their code lengths.
 __global__ void __launch_bounds__(256) huff_sizes_kernel(const uint8_t *in, uint64_t n,
                                                         uint8_t *out, const uint32_t *book) {
   __shared__ uint8_t len[256];
@@ -235,27 +260,33 @@ __global__ void __launch_bounds__(256) huff_sizes_kernel(const uint8_t *in, uint
   const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
   uint32_t *subs = reinterpret_cast<uint32_t *>(out + huf_subs_at(nb));
   unsigned long long *table = reinterpret_cast<unsigned long long *>(out + kHufTableAt);
-  const bool aligned = (reinterpret_cast<uintptr_t>(in) & 3u) == 0;
+  const bool in16 = (reinterpret_cast<uintptr_t>(in) & 15u) == 0;
   for (uint64_t b = gw; b < nb; b += nw) {
-    uint64_t lo, hi;
-    sub_range(b, lane, n, lo, hi);
-    uint32_t bits = 0;
-    uint64_t i = lo;
-    if (aligned) {
-      const uint32_t *w32 = reinterpret_cast<const uint32_t *>(in);
-      for (; i + 4 <= hi; i += 4) {
-        const uint32_t v = w32[i / 4];
-        bits += len[v & 0xFF] + len[(v >> 8) & 0xFF] + len[(v >> 16) & 0xFF] + len[v >> 24];
-      }
+    uint32_t mine = 0;  // bits of sub-block `lane`
+    for (uint32_t sb = 0; sb < kHufSubs; ++sb) {
+      uint64_t lo, hi;
+      sub_range(b, sb, n, lo, hi);
+      if (lo >= hi) break;  // every later sub-block is empty too
+      uint32_t w[8];
+      lane_bytes(in, lo + 32ull * lane, hi, in16, w);
+      const uint32_t valid = lo + 32ull * lane >= hi ? 0u
+                             : static_cast<uint32_t>(min(hi - lo - 32ull * lane, 32ull));
+      uint32_t bits = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          bits += (4u * q + k < valid) ? len[(w[q] >> (8 * k)) & 0xFF] : 0u;
+      const uint32_t total = __reduce_add_sync(kFull, bits);
+      if (lane == sb) mine = total;
     }
-    for (; i < hi; ++i) bits += len[in[i]];
-    uint32_t incl = bits;
+    uint32_t incl = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(kFull, incl, o);
       if (lane >= static_cast<uint32_t>(o)) incl += y;
     }
-    subs[b * kHufSubs + lane] = incl - bits;
+    subs[b * kHufSubs + lane] = incl - mine;
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     if (lane == 0) table[b] = static_cast<unsigned long long>((total + 31) / 32) * 4;  // size
   }
@@ -297,13 +328,23 @@ __global__ void __launch_bounds__(1024) huff_scan_kernel(uint8_t *out, uint64_t 
   }
 }
 
+// Encoding, one warp per block.  Sub-block by sub-block, each lane codes
+// 32 consecutive bytes; a warp scan of the lanes' bit counts places each
+// lane's codes, which are ORed into a per-warp shared-memory copy of the
+// sub-block's words.  The complete words go out with coalesced stores; a
+// last, partial word carries over to the next sub-block (or is written at
+// the end of the block), so every word of the bit string is written once.
+constexpr uint32_t kEncWords = (kHufSub * kHufMaxLen) / 32 + 2;  // words of one sub-block
+
 __global__ void __launch_bounds__(256) huff_encode_kernel(const uint8_t *in, uint64_t n,
                                                          uint8_t *out, uint64_t out_cap,
                                                          const uint32_t *book) {
   __shared__ uint32_t cl[256];  // code | length << 24
+  __shared__ uint32_t sbuf[8][kEncWords];
   for (uint32_t s = threadIdx.x; s < 256; s += blockDim.x) cl[s] = book[s];
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31;
+  uint32_t *wb = sbuf[threadIdx.x >> 5];
   const uint64_t nb = (n + kHufBlock - 1) / kHufBlock;
   const uint64_t gw = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -311,52 +352,76 @@ __global__ void __launch_bounds__(256) huff_encode_kernel(const uint8_t *in, uin
   const uint32_t *subs = reinterpret_cast<const uint32_t *>(out + huf_subs_at(nb));
   const unsigned long long *table =
       reinterpret_cast<const unsigned long long *>(out + kHufTableAt);
-  const bool aligned = (reinterpret_cast<uintptr_t>(in) & 3u) == 0;
+  const bool in16 = (reinterpret_cast<uintptr_t>(in) & 15u) == 0;
   for (uint64_t b = gw; b < nb; b += nw) {
     const uint64_t start = b ? table[b - 1] : 0ull, end = table[b];
     if (bits_at + end > out_cap) continue;  // reported by the scan kernel
     uint32_t *w32 = reinterpret_cast<uint32_t *>(out + bits_at + start);
-    const uint32_t bytes = static_cast<uint32_t>(end - start);
-    uint64_t lo, hi;
-    sub_range(b, lane, n, lo, hi);
-    const uint32_t o = subs[b * kHufSubs + lane];
-    // words that other lanes (or the padding) share are cleared first: each
-    // non-empty lane's first word and the block's last word
-    if (hi > lo) w32[o / 32] = 0;
-    if (lane == 0 && bytes) w32[bytes / 4 - 1] = 0;
-    __syncwarp();
-    uint64_t acc = 0;
-    uint32_t nacc = o % 32, wi = o / 32;
-    bool shared = nacc != 0;  // the current word holds an earlier lane's bits
-    uint64_t i = lo;
-    auto put = [&](uint32_t sym) {
-      const uint32_t c = cl[sym];
-      const uint32_t l = c >> 24;
-      acc = (acc << l) | (c & 0xFFFFFFu);
-      nacc += l;
-      if (nacc >= 32) {
-        nacc -= 32;
-        const uint32_t word = static_cast<uint32_t>(acc >> nacc);
-        if (shared) atomicOr(&w32[wi], word);
-        else w32[wi] = word;
-        shared = false;
-        ++wi;
-        acc &= (1ull << nacc) - 1ull;
+    uint32_t carry = 0;     // bits already placed in word `at / 32` (the partial word)
+    uint32_t at = 0;        // bit position in the block after the last sub-block
+    for (uint32_t sb = 0; sb < kHufSubs; ++sb) {
+      uint64_t lo, hi;
+      sub_range(b, sb, n, lo, hi);
+      if (lo >= hi) break;
+      const uint32_t a = subs[b * kHufSubs + sb];  // == at
+      uint32_t w[8];
+      lane_bytes(in, lo + 32ull * lane, hi, in16, w);
+      const uint32_t valid = lo + 32ull * lane >= hi ? 0u
+                             : static_cast<uint32_t>(min(hi - lo - 32ull * lane, 32ull));
+      uint32_t bits = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          bits += (4u * q + k < valid) ? (cl[(w[q] >> (8 * k)) & 0xFF] >> 24) : 0u;
+      uint32_t incl = bits;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= static_cast<uint32_t>(o)) incl += y;
       }
-    };
-    if (aligned) {
-      const uint32_t *in32 = reinterpret_cast<const uint32_t *>(in);
-      for (; i + 4 <= hi; i += 4) {
-        const uint32_t v = in32[i / 4];
-        put(v & 0xFF);
-        put((v >> 8) & 0xFF);
-        put((v >> 16) & 0xFF);
-        put(v >> 24);
-      }
+      const uint32_t sub_bits = __shfl_sync(kFull, incl, 31);
+      const uint32_t r0 = a % 32;                      // bits of the carried word
+      const uint32_t nwords = (r0 + sub_bits + 31) / 32;
+      for (uint32_t k = lane; k < nwords; k += 32) wb[k] = 0;
+      __syncwarp();
+      if (lane == 0 && r0) wb[0] = carry;
+      __syncwarp();
+      // this lane's codes, most significant bit first, from bit r0 + excl
+      uint32_t p = r0 + incl - bits;
+      uint64_t acc = 0;
+      uint32_t nacc = p % 32, wi = p / 32;
+      bool first = true;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (4u * q + k < valid) {
+            const uint32_t c = cl[(w[q] >> (8 * k)) & 0xFF];
+            const uint32_t l = c >> 24;
+            acc = (acc << l) | (c & 0xFFFFFFu);
+            nacc += l;
+            if (nacc >= 32) {
+              nacc -= 32;
+              const uint32_t word = static_cast<uint32_t>(acc >> nacc);
+              if (first) atomicOr(&wb[wi], word);  // shared with the lane before
+              else wb[wi] = word;
+              first = false;
+              ++wi;
+              acc &= (1ull << nacc) - 1ull;
+            }
+          }
+        }
+      if (nacc > 0 && bits > 0) atomicOr(&wb[wi], static_cast<uint32_t>(acc << (32 - nacc)));
+      __syncwarp();
+      // complete words out; a partial last word stays for the next sub-block
+      const uint32_t full = (r0 + sub_bits) / 32;
+      for (uint32_t k = lane; k < full; k += 32) w32[a / 32 + k] = wb[k];
+      carry = (r0 + sub_bits) % 32 ? wb[full] : 0u;
+      __syncwarp();
+      at = a + sub_bits;
     }
-    for (; i < hi; ++i) put(in[i]);
-    if (nacc > 0 && hi > lo) atomicOr(&w32[wi], static_cast<uint32_t>(acc << (32 - nacc)));
-    __syncwarp();
+    if (at % 32 && lane == 0) w32[at / 32] = carry;  // the block's last, padded word
   }
 }
 
@@ -422,9 +487,29 @@ __global__ void __launch_bounds__(256) huff_decode_kernel(const uint8_t *in, uin
     return;
   }
   canonical_codes(len, first, cnt, code);
-  if (t < 256 && len[t]) {
-    const uint32_t l = len[t], lo = code[t] << (kHufMaxLen - l), hi = (code[t] + 1) << (kHufMaxLen - l);
-    for (uint32_t e = lo; e < hi; ++e) dec[e] = static_cast<uint16_t>(t | (l << 8));
+  // symbols in canonical order: those of length l hold places off[l] ..
+  // off[l] + cnt[l] - 1, by value
+  __shared__ uint32_t off[kHufMaxLen + 2];
+  __shared__ uint8_t order[256];
+  if (t == 0) {
+    off[1] = 0;
+    for (uint32_t l = 1; l <= kHufMaxLen; ++l) off[l + 1] = off[l] + cnt[l];
+  }
+  __syncthreads();
+  if (t < 256 && len[t]) order[off[len[t]] + code[t] - first[len[t]]] = static_cast<uint8_t>(t);
+  __syncthreads();
+  // entry e (the next 12 bits) belongs to the length l whose codes cover
+  // e >> (12 - l); each thread fills 16 entries
+  for (uint32_t e = t; e < (1u << kHufMaxLen); e += blockDim.x) {
+    uint16_t v = kHufInvalid;
+    for (uint32_t l = 1; l <= kHufMaxLen; ++l) {
+      const uint32_t c = e >> (kHufMaxLen - l);
+      if (cnt[l] && c >= first[l] && c - first[l] < cnt[l]) {
+        v = static_cast<uint16_t>(order[off[l] + c - first[l]] | (l << 8));
+        break;
+      }
+    }
+    dec[e] = v;
   }
   __syncthreads();
 
@@ -433,7 +518,7 @@ __global__ void __launch_bounds__(256) huff_decode_kernel(const uint8_t *in, uin
   const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
   const uint32_t *subs = reinterpret_cast<const uint32_t *>(in + huf_subs_at(h.nb));
   const uint8_t *table = in + kHufTableAt;
-  const bool out_aligned = (reinterpret_cast<uintptr_t>(out) & 3u) == 0;
+  const bool out16 = (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
   for (uint64_t b = gw; b < h.nb; b += nw) {
     const uint64_t start = b ? ld_u64_le(table + 8 * (b - 1)) : 0ull;
     const uint64_t end = ld_u64_le(table + 8 * b);
@@ -452,44 +537,51 @@ __global__ void __launch_bounds__(256) huff_decode_kernel(const uint8_t *in, uin
     }
     const uint32_t *w32 = reinterpret_cast<const uint32_t *>(in + h.bits_at + start);
     const uint32_t nwords = static_cast<uint32_t>(bytes / 4);
-    // a 64-bit window over words ci, ci + 1; r = bit position inside it
-    uint32_t ci = o / 32, r = o % 32;
-    auto word = [&](uint32_t k) -> uint64_t { return k < nwords ? w32[k] : 0u; };
-    uint64_t win = (word(ci) << 32) | word(ci + 1);
+    // bit buffer: the next `avail` (>= 32 after a refill) bits, left-aligned;
+    // `nextw` is the word after them, loaded one refill ahead
+    uint32_t wi = o / 32;
+    uint64_t buf = (static_cast<uint64_t>(wi < nwords ? w32[wi] : 0u) << 32) |
+                   (wi + 1 < nwords ? w32[wi + 1] : 0u);
+    buf <<= o % 32;
+    uint32_t avail = 64 - o % 32;
+    wi += 2;
+    uint32_t nextw = wi < nwords ? w32[wi] : 0u;
     uint32_t pos = o;
-    bool lane_bad = false;
-    uint32_t pack = 0;
-    for (uint64_t i = lo; i < hi; ++i) {
-      const uint32_t e = dec[static_cast<uint32_t>((win << r) >> (64 - kHufMaxLen))];
-      const uint32_t l = e >> 8;
-      if (e == kHufInvalid || pos + l > nbits) {
-        lane_bad = true;
-        break;
-      }
+    bool invalid = false;
+    auto next_symbol = [&]() -> uint32_t {
+      const uint32_t e = dec[static_cast<uint32_t>(buf >> (64 - kHufMaxLen))];
+      const uint32_t l = (e >> 8) & 15u;  // an invalid entry reads as length 15
+      invalid |= e == kHufInvalid;
+      buf <<= l;
+      avail -= l;
       pos += l;
-      r += l;
-      if (r >= 32) {
-        r -= 32;
-        ++ci;
-        win = (win << 32) | word(ci + 1);
+      if (avail < 32) {
+        buf |= static_cast<uint64_t>(nextw) << (32 - avail);
+        avail += 32;
+        ++wi;
+        nextw = wi < nwords ? w32[wi] : 0u;
       }
-      const uint32_t sym = e & 0xFF;
-      if (out_aligned) {
-        pack |= sym << (8 * (i & 3));
-        if ((i & 3) == 3) {
-          reinterpret_cast<uint32_t *>(out)[i / 4] = pack;
-          pack = 0;
+      return e & 0xFFu;
+    };
+    uint64_t i = lo;
+    if (out16) {
+      for (; i + 16 <= hi; i += 16) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          uint32_t v = next_symbol();
+          v |= next_symbol() << 8;
+          v |= next_symbol() << 16;
+          v |= next_symbol() << 24;
+          w[q] = v;
         }
-      } else {
-        out[i] = static_cast<uint8_t>(sym);
+        *reinterpret_cast<uint4 *>(out + i) = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
-    if (!lane_bad && out_aligned && (hi & 3) && hi > lo) {
-      for (uint64_t i = hi & ~3ull; i < hi; ++i)
-        out[i] = static_cast<uint8_t>(pack >> (8 * (i & 3)));
-    }
+    for (; i < hi; ++i) out[i] = static_cast<uint8_t>(next_symbol());
     // each sub-block ends where the next begins; the block's words hold
     // exactly the bits used, rounded up to a word
+    bool lane_bad = invalid || pos > nbits;
     if (lane < 31) lane_bad = lane_bad || pos != o_next;
     else lane_bad = lane_bad || (pos + 31) / 32 != nwords;
     if (__any_sync(kFull, lane_bad) && lane == 0) atomicOr(err, kErrCorrupt);
