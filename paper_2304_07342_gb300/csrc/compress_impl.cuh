@@ -819,6 +819,7 @@ struct WarpState {
   uint64_t *bar;
   uint32_t phase;
   uint32_t slot_c, slot_item, slot_rec;
+  bool try_literal;  // the warp's previous chunk was all literals
 };
 
 // Parking slots of this warp whose chunk can now be placed are placed and
@@ -876,6 +877,7 @@ __device__ __forceinline__ void init_warp_state(const CompressArgs &A, uint8_t *
   W.slot_c = kFreeSlot;
   W.slot_item = 0;
   W.slot_rec = 0;
+  W.try_literal = true;
 }
 
 __device__ __forceinline__ void write_header(const BufDesc &B, uint32_t lane) {
@@ -942,7 +944,10 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
   // payload staging area)
   const uint32_t bl = 31u - __clz(A.sm.pay_bytes / 4);  // bitmap words = 2^bl
   bool literal = false;
-  if (bl >= 2 && (2u << bl) >= k)
+  // (tried when this warp's previous chunk was all literals: on data with
+  // repeats the check would only give up, so it is not tried again until a
+  // chunk without a match comes by)
+  if (W.try_literal && bl >= 2 && (2u << bl) >= k)
     literal = literal_chunk<S>(sym, k, B, reinterpret_cast<uint32_t *>(W.pay), bl, W.maybe,
                                lane);
   uint32_t marked = 0;
@@ -966,6 +971,7 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
     payload = W.pay;
   }
   if (!sane && lane == 0) atomicOr(A.err, kErrInternal);
+  W.try_literal = payload == W.inb;  // no pointer in this chunk
   // stream version 2, last chunk: the 1..S-1 bytes after the last whole
   // symbol follow the tokens as they are (in the staged chunk they already
   // follow the k symbols)
