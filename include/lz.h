@@ -19,7 +19,9 @@
  * lz_compress_ex on request, adds stored chunks and tail bytes, see
  * lz_options):
  *   header  32 B: "GLZ1", u8 version (1 or 2), u8 S, u8 offB, u8 m, u8 M,
- *           3 zero bytes, u32 chunk_bytes, u32 W, u32 n_chunks, u64 n_bytes
+ *           u8 overlap (version 2: 1 when pointers may be longer than their
+ *           offset, else 0), 2 zero bytes, u32 chunk_bytes, u32 W,
+ *           u32 n_chunks, u64 n_bytes
  *   table   n_chunks x {u32 n_tokens, u32 payload_bytes}
  *   index   ceil(n_chunks/64) x u64: offset of the record of chunk 64*j,
  *           relative to the start of the records region
@@ -67,11 +69,16 @@ typedef struct lz_params {
 typedef enum lz_match {
   LZ_MATCH_EXACT = 0, /* longest match, nearest offset on ties (section 2.2
                          step 2, the definition; what lz_compress uses)   */
-  LZ_MATCH_PAPER = 1  /* the paper's own matcher (section 3.3.2, the four
+  LZ_MATCH_PAPER = 1,  /* the paper's own matcher (section 3.3.2, the four
                          steps of its matching method): a forward scan of
                          the window from its far end whose search pointer
                          never moves back, keeping the first run of the
                          greatest length; it can miss the longest match */
+  LZ_MATCH_OVERLAP = 2 /* the exact longest match when a match may run on
+                         into the symbols it produces (length bounded by M
+                         and the chunk end, not by the offset; classic LZ77,
+                         which section 3.3.2 does not use); stream version 2
+                         only, recorded in header byte 9 */
 } lz_match;
 
 typedef enum lz_status {
@@ -149,8 +156,9 @@ typedef struct lz_options {
  * symbols; the parse takes a pointer when the kept run has >= m symbols.
  * Positions without any match of >= m symbols are literals under both
  * matchers, and the stream header does not record the matcher.
- * LZ_ERR_INVALID_ARG for an unknown matcher or version, or for
- * n_bytes % S != 0 in version 1; everything else as for lz_compress
+ * LZ_ERR_INVALID_ARG for an unknown matcher or version, for LZ_MATCH_OVERLAP
+ * in version 1, or for n_bytes % S != 0 in version 1; everything else as
+ * for lz_compress
  * (lz_compressed_bound covers both versions, a tail included). */
 lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
                          const lz_params *p, const lz_options *opt, void *d_out,

@@ -92,6 +92,9 @@ def _load():
         lib.lzref_compress_v.argtypes = [u8p, u64] + [u32] * 7 + [
             u8p, u64, u64p]
         lib.lzref_compress_v.restype = ctypes.c_int
+        lib.lzref_longest_match_overlap.argtypes = [u8p, u32, u32, u32, u32, u32,
+                                                    u32p, u32p]
+        lib.lzref_longest_match_overlap.restype = None
         lib.huffref_lengths.argtypes = [u64p, u32, u8p]
         lib.huffref_lengths.restype = None
         lib.huffref_codes.argtypes = [u8p, u32p]
@@ -155,6 +158,17 @@ def longest_match(chunk, p_sym: int, S: int, W: int, M: int = 255):
     return ln.value, off.value
 
 
+def longest_match_overlap(chunk, p_sym: int, S: int, W: int, M: int = 255):
+    """(len, off) of the longest, nearest match at ``p_sym`` when matches may
+    overlap the look-ahead (length bounded by M and the chunk end only)."""
+    b = _bytes(chunk)
+    k = b.size // S
+    ln, off = ctypes.c_uint32(), ctypes.c_uint32()
+    _load().lzref_longest_match_overlap(_ptr(b), k, p_sym, S, W, M,
+                                        ctypes.byref(ln), ctypes.byref(off))
+    return ln.value, off.value
+
+
 def paper_match(chunk, p_sym: int, S: int, W: int, M: int = 255):
     """(len, off) found at symbol ``p_sym`` by the paper's matcher (section
     3.3.2: forward scan, search pointer never moved back, first run of the
@@ -167,7 +181,7 @@ def paper_match(chunk, p_sym: int, S: int, W: int, M: int = 255):
     return ln.value, off.value
 
 
-MATCH_EXACT, MATCH_PAPER = 0, 1
+MATCH_EXACT, MATCH_PAPER, MATCH_OVERLAP = 0, 1, 2
 
 
 def parse_chunk(chunk, S: int, W: int, m: int, M: int = 255,

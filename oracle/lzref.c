@@ -142,11 +142,37 @@ void lzref_paper_match(const uint8_t *chunk, uint32_t k, uint32_t p,
   *off = best_off;
 }
 
+/* The exact longest match when a match may overlap the look-ahead (stream
+ * version 2's overlap mode): as lzref_longest_match, but a match may run on
+ * into the symbols it produces, so its length is bounded by M and by the
+ * symbols left in the chunk only (the classic LZ77 reading; section 3.3.2
+ * forbids it for the paper's own format).  Nearest offset on ties. */
+void lzref_longest_match_overlap(const uint8_t *chunk, uint32_t k, uint32_t p,
+                                 uint32_t S, uint32_t W, uint32_t M,
+                                 uint32_t *len, uint32_t *off) {
+  uint32_t best = 0, best_d = 0;
+  uint32_t dmax = W < p ? W : p;
+  for (uint32_t d = 1; d <= dmax; ++d) {
+    uint32_t cap = M;
+    if (k - p < cap) cap = k - p;
+    uint32_t l = 0;
+    while (l < cap && ref_sym_eq(chunk, S, p + l, p - d + l)) ++l;
+    if (l > best) {
+      best = l;
+      best_d = d;
+    }
+  }
+  *len = best;
+  *off = best_d;
+}
+
 typedef void (*ref_matcher)(const uint8_t *, uint32_t, uint32_t, uint32_t,
                             uint32_t, uint32_t, uint32_t *, uint32_t *);
 
 static ref_matcher ref_matcher_of(uint32_t mode) {
-  return mode == LZREF_MATCH_PAPER ? lzref_paper_match : lzref_longest_match;
+  if (mode == LZREF_MATCH_PAPER) return lzref_paper_match;
+  if (mode == LZREF_MATCH_OVERLAP) return lzref_longest_match_overlap;
+  return lzref_longest_match;
 }
 
 /* Section 2.2 steps 1, 3, 4, 6: greedy parse from the chunk start. */
@@ -215,8 +241,11 @@ int lzref_compress_v(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
                      uint32_t version, uint8_t *out, uint64_t cap,
                      uint64_t *out_bytes) {
   if (lzref_check_params(S, C, W, m, M) != REF_OK) return REF_EINVAL;
-  if (mode != LZREF_MATCH_EXACT && mode != LZREF_MATCH_PAPER) return REF_EINVAL;
+  if (mode != LZREF_MATCH_EXACT && mode != LZREF_MATCH_PAPER &&
+      mode != LZREF_MATCH_OVERLAP)
+    return REF_EINVAL;
   if (version != 1 && version != 2) return REF_EINVAL;
+  if (mode == LZREF_MATCH_OVERLAP && version != 2) return REF_EINVAL;
   if (version == 1 && n % S != 0) return REF_EINVAL;
   uint64_t nc = ref_div_up(n, C);
   if (nc > 0xFFFFFFFFull) return REF_EINVAL;
@@ -230,6 +259,7 @@ int lzref_compress_v(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
   memset(out, 0, (size_t)records_at);
   memcpy(out, "GLZ1", 4);
   out[4] = (uint8_t)version;
+  out[9] = mode == LZREF_MATCH_OVERLAP ? 1u : 0u; /* overlap flag (version 2) */
   out[5] = (uint8_t)S;
   out[6] = (uint8_t)offB;
   out[7] = (uint8_t)m;
@@ -324,7 +354,7 @@ static int ref_read_header(const uint8_t *in, uint64_t in_bytes,
                            uint64_t *nc, uint64_t *n) {
   if (in_bytes < REF_HEADER_BYTES) return REF_ECORRUPT;
   if (memcmp(in, "GLZ1", 4) != 0 || (in[4] != 1 && in[4] != 2)) return REF_ECORRUPT;
-  if (in[9] || in[10] || in[11]) return REF_ECORRUPT;
+  if (in[9] > (in[4] == 2 ? 1 : 0) || in[10] || in[11]) return REF_ECORRUPT;
   *S = in[5];
   *offB = in[6];
   *m = in[7];
@@ -399,6 +429,7 @@ int lzref_decompress(const uint8_t *in, uint64_t in_bytes, uint8_t *out,
         /* an offset reaches at most W symbols back (section 2.2 sliding window)
          and never before the chunk start */
         if (len == 0 || off > p || off > W || len > k - p) return REF_ECORRUPT;
+        if (len > off && !in[9]) return REF_ECORRUPT; /* overlap only if flagged */
         for (uint32_t i = 0; i < len; ++i)
           memcpy(dst + (size_t)(p + i) * S, dst + (size_t)(p + i - off) * S,
                  S);

@@ -62,9 +62,16 @@ void lzref_paper_match(const uint8_t *chunk, uint32_t k, uint32_t p,
                        uint32_t S, uint32_t W, uint32_t M, uint32_t *len,
                        uint32_t *off);
 
+/* The exact longest match with overlapping allowed (length bounded by M
+ * and k - p only, not by the offset); nearest offset on ties. */
+void lzref_longest_match_overlap(const uint8_t *chunk, uint32_t k, uint32_t p,
+                                 uint32_t S, uint32_t W, uint32_t M,
+                                 uint32_t *len, uint32_t *off);
+
 /* Matchers of the greedy parse. */
-#define LZREF_MATCH_EXACT 0u /* lzref_longest_match (the definition) */
-#define LZREF_MATCH_PAPER 1u /* lzref_paper_match (the paper's method) */
+#define LZREF_MATCH_EXACT 0u   /* lzref_longest_match (the definition) */
+#define LZREF_MATCH_PAPER 1u   /* lzref_paper_match (the paper's method) */
+#define LZREF_MATCH_OVERLAP 2u /* lzref_longest_match_overlap; version 2 */
 
 /* Greedy parse of one chunk.  tok_len[t] = symbols covered by token t,
  * tok_off[t] = pointer offset in symbols (0 for a literal).  Arrays must
@@ -97,7 +104,10 @@ int lzref_compress_mode(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
  *      so a token count of 0 marks a stored chunk unambiguously.  n need
  *      not be a multiple of S: the last chunk's 1..S-1 bytes past its last
  *      whole symbol follow its payload as they are (counted in
- *      payload_bytes), and a chunk with no whole symbol is stored.
+ *      payload_bytes), and a chunk with no whole symbol is stored.  Header
+ *      byte 9 is 1 when the stream was parsed with LZREF_MATCH_OVERLAP
+ *      (pointers may be longer than their offset), else 0; the decoders
+ *      reject a pointer longer than its offset in a stream without it.
  * The decoder reads both versions. */
 int lzref_compress_v(const uint8_t *in, uint64_t n, uint32_t S, uint32_t C,
                      uint32_t W, uint32_t m, uint32_t M, uint32_t mode,

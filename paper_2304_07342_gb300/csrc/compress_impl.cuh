@@ -243,12 +243,14 @@ __device__ __forceinline__ bool match_near(const typename SymType<S>::T *sym, ui
   bool hit = false;
   for (uint32_t d0 = 0; d0 < dmax; d0 += 32) {
     const uint32_t d = d0 + lane + 1;
-    bool eq = d >= A.m && d <= dmax;
+    // a match of >= m symbols needs offset >= m unless matches may overlap
+    bool eq = (d >= A.m || A.match == kMatchOverlap) && d <= dmax;
     for (uint32_t i = 0; eq && i < A.m; ++i) eq = sym[p + i] == sym[p - d + i];
     hit |= eq;
   }
   const uint32_t q = p + 1 + lane;
-  bool eq = q < slab_end && q - p >= A.m && q - p <= A.W && q + A.m <= k;
+  bool eq = q < slab_end && (q - p >= A.m || A.match == kMatchOverlap) && q - p <= A.W &&
+            q + A.m <= k;
   for (uint32_t i = 0; eq && i < A.m; ++i) eq = sym[q + i] == sym[p + i];
   hit |= eq;
   return __any_sync(kFull, hit);
@@ -364,6 +366,7 @@ __device__ __forceinline__ bool chain_match(const typename SymType<S>::T *sym,
                                             uint32_t k, const BufDesc &A,
                                             const Links<WIDE> &links, uint32_t q,
                                             uint32_t &best, uint32_t &bd) {
+  const bool overlap = A.match == kMatchOverlap;  // lengths not bounded by the offset
   const uint32_t lim = min(A.M, k - q);
   best = 0;
   bd = 0;
@@ -371,8 +374,8 @@ __device__ __forceinline__ bool chain_match(const typename SymType<S>::T *sym,
   while (d != 0 && d <= A.W) {
     if (best == lim) return true;
     if (hops >= kChainHops || work >= kChainWork) return false;
-    if (d >= A.m) {
-      const uint32_t cap = min(lim, d);
+    if (overlap || d >= A.m) {
+      const uint32_t cap = overlap ? lim : min(lim, d);
       // only a candidate that agrees at index `best` can be longer
       if (cap > best && sym[q + best] == sym[q - d + best]) {
         const uint32_t l = extend_words<S>(reinterpret_cast<const uint8_t *>(sym), q, d, cap);
@@ -474,8 +477,9 @@ __device__ __forceinline__ void window_match(const typename SymType<S>::T *sym,
       const int idx = static_cast<int>(p + L) - static_cast<int>(lane + 1 + 32 * j);
       eq |= static_cast<uint32_t>(sym[idx < 0 ? 0 : idx] == c) << j;
     }
+    // offsets d <= L drop out (length <= offset) unless matches may overlap
     const uint32_t jmin = (L > lane) ? ((L - lane - 1) >> 5) + 1 : 0;
-    const uint32_t capm = jmin >= 32 ? 0u : (kFull << jmin);
+    const uint32_t capm = A.match == kMatchOverlap ? kFull : (jmin >= 32 ? 0u : (kFull << jmin));
     const uint32_t nxt = alive & eq & capm;
     if (!__any_sync(kFull, nxt != 0)) break;
     alive = nxt;
@@ -892,6 +896,7 @@ __device__ __forceinline__ void write_header(const BufDesc &B, uint32_t lane) {
     case 6: b = B.offB; break;
     case 7: b = B.m; break;
     case 8: b = B.M; break;
+    case 9: b = B.match == kMatchOverlap ? 1u : 0u; break;  // overlap flag (version 2)
     default:
       if (lane >= 12 && lane < 16) b = B.C >> (8 * (lane - 12));
       else if (lane >= 16 && lane < 20) b = B.W >> (8 * (lane - 16));

@@ -33,15 +33,16 @@ namespace glz {
 namespace {
 
 struct Header {
-  uint32_t version, S, offB, m, M, C, W, nc;
+  uint32_t version, overlap, S, offB, m, M, C, W, nc;
   uint64_t n;
 };
 
 __device__ __forceinline__ bool read_header(const uint8_t *in, Header &h) {
   const bool magic = in[0] == 'G' && in[1] == 'L' && in[2] == 'Z' &&
-                     in[3] == '1' && (in[4] == 1 || in[4] == 2) && in[9] == 0 &&
-                     in[10] == 0 && in[11] == 0;
+                     in[3] == '1' && (in[4] == 1 || in[4] == 2) &&
+                     in[9] <= (in[4] == 2 ? 1 : 0) && in[10] == 0 && in[11] == 0;
   h.version = in[4];
+  h.overlap = in[9];  // version 2: pointers may be longer than their offset
   h.S = in[5];
   h.offB = in[6];
   h.m = in[7];
@@ -249,7 +250,7 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
         val = static_cast<uint32_t>(ld_le(payload + my_off, S));
       }
     }
-    tbad = tbad || (ism && (len == 0 || off > h.W));
+    tbad = tbad || (ism && (len == 0 || off > h.W || (len > off && !h.overlap)));
     // inclusive scan of token lengths -> output start of each token
     uint32_t x = len;
 #pragma unroll

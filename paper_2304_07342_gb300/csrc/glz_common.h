@@ -15,6 +15,7 @@ constexpr uint32_t kMaxWindow = 1024;   // symbols
 // Matchers of the greedy parse (lz_match in lz.h).
 constexpr uint32_t kMatchExact = 0;  // longest match, nearest offset on ties
 constexpr uint32_t kMatchPaper = 1;  // the paper's forward scan (section 3.3.2)
+constexpr uint32_t kMatchOverlap = 2;  // exact, a match may overlap its output
 
 // Sticky device error bits (lz_sync maps them back to lz_status).
 constexpr uint32_t kErrSmall = 1u << 0;
@@ -50,7 +51,7 @@ struct BufDesc {
   uint32_t S, C, W, m, M, offB;
   uint32_t nc;          // chunks
   uint32_t in_aligned;  // in is 16-byte aligned: TMA bulk staging
-  uint32_t match;       // kMatchExact or kMatchPaper
+  uint32_t match;       // kMatchExact, kMatchPaper or kMatchOverlap
   uint32_t version;     // stream version written: 1, or 2 (stored chunks); 0 reads as 1
   uint64_t records_at;  // byte offset of the records region
   uint64_t gbase;       // index of this buffer's chunk 0 among all chunks

@@ -260,8 +260,10 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
   if (!ctx || !params_ok(p) || !d_out || !d_out_bytes) return LZ_ERR_INVALID_ARG;
   const uint32_t match = opt ? opt->match : LZ_MATCH_EXACT;
   const uint32_t version = opt && opt->version ? opt->version : 1u;
-  if (match != LZ_MATCH_EXACT && match != LZ_MATCH_PAPER) return LZ_ERR_INVALID_ARG;
+  if (match != LZ_MATCH_EXACT && match != LZ_MATCH_PAPER && match != LZ_MATCH_OVERLAP)
+    return LZ_ERR_INVALID_ARG;
   if (version != 1 && version != 2) return LZ_ERR_INVALID_ARG;
+  if (match == LZ_MATCH_OVERLAP && version != 2) return LZ_ERR_INVALID_ARG;
   if (n_bytes > 0 && !d_in) return LZ_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(d_out_bytes) % 8 != 0) return LZ_ERR_INVALID_ARG;
   const uint32_t S = p->symbol_bytes, C = p->chunk_bytes;
@@ -326,7 +328,9 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
   A.buf.nc = static_cast<uint32_t>(nc);
   A.buf.records_at = records_at;
   A.buf.in_aligned = (reinterpret_cast<uintptr_t>(d_in) % 16) == 0;
-  A.buf.match = match == LZ_MATCH_PAPER ? glz::kMatchPaper : glz::kMatchExact;
+  A.buf.match = match == LZ_MATCH_PAPER     ? glz::kMatchPaper
+                : match == LZ_MATCH_OVERLAP ? glz::kMatchOverlap
+                                            : glz::kMatchExact;
   A.buf.version = version;
   A.buf.gbase = 0;
   A.total_chunks = nc;
@@ -365,7 +369,7 @@ lz_status lz_decompressed_size(const void *d_in, uint64_t in_bytes,
   uint64_t n = 0;
   for (int i = 0; i < 8; ++i) n |= static_cast<uint64_t>(h[24 + i]) << (8 * i);
   lz_params p{h[5], u32(12), u32(16), h[7], h[8]};
-  if (std::memcmp(h, "GLZ1", 4) != 0 || (h[4] != 1 && h[4] != 2) || h[9] || h[10] || h[11] ||
+  if (std::memcmp(h, "GLZ1", 4) != 0 || (h[4] != 1 && h[4] != 2) || h[9] > (h[4] == 2 ? 1 : 0) || h[10] || h[11] ||
       !params_ok(&p) || h[6] != off_bytes(p.window) || (h[4] == 1 && n % p.symbol_bytes != 0) ||
       u32(20) != div_up(n, p.chunk_bytes))
     return LZ_ERR_CORRUPT;
@@ -831,7 +835,7 @@ lz_status batch_create_decompress(lz_ctx *ctx, const lz_batch_item *items, uint3
                 static_cast<uint32_t>(header_u(h, 16, 4)), h[7], h[8]};
     const uint64_t nn = header_u(h, 24, 8);
     const uint64_t nc = header_u(h, 20, 4);
-    if (std::memcmp(h, "GLZ1", 4) != 0 || (h[4] != 1 && h[4] != 2) || h[9] || h[10] || h[11] ||
+    if (std::memcmp(h, "GLZ1", 4) != 0 || (h[4] != 1 && h[4] != 2) || h[9] > (h[4] == 2 ? 1 : 0) || h[10] || h[11] ||
         !params_ok(&p) || h[6] != off_bytes(p.window) || (h[4] == 1 && nn % p.symbol_bytes != 0) ||
         nc != div_up(nn, p.chunk_bytes))
       return LZ_ERR_CORRUPT;

@@ -26,6 +26,7 @@ LZ_ERR_INTERNAL = 7
 
 LZ_MATCH_EXACT = 0  # longest match, nearest offset on ties (the definition)
 LZ_MATCH_PAPER = 1  # the paper's forward scan (section 3.3.2)
+LZ_MATCH_OVERLAP = 2  # exact, matches may overlap their output (stream version 2)
 
 _NAMES = {0: "LZ_OK", 1: "LZ_ERR_INVALID_ARG", 2: "LZ_ERR_BUFFER_TOO_SMALL",
           3: "LZ_ERR_CORRUPT", 4: "LZ_ERR_NOMEM", 5: "LZ_ERR_CUDA",

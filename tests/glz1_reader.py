@@ -29,17 +29,19 @@ class Stream:
     stored: list = field(default_factory=list)     # per chunk: stored as is (version 2)
     total_bytes: int = 0
     version: int = 1
+    overlap: bool = False
 
 
 def read(buf: bytes) -> Stream:
     buf = bytes(buf)
     assert buf[:4] == b"GLZ1", "magic"
     ver, S, offB, m, M = buf[4], buf[5], buf[6], buf[7], buf[8]
-    assert ver in (1, 2) and buf[9:12] == b"\0\0\0"
+    assert ver in (1, 2) and buf[9] <= (1 if ver == 2 else 0) and buf[10:12] == b"\0\0"
     C, W, nc = struct.unpack_from("<III", buf, 12)
     (n,) = struct.unpack_from("<Q", buf, 24)
     st = Stream(S, offB, m, M, C, W, nc, n)
     st.version = ver
+    st.overlap = buf[9] == 1
     pos = 32
     for c in range(nc):
         st.table.append(struct.unpack_from("<II", buf, pos))

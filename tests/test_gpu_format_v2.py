@@ -125,3 +125,36 @@ def test_v2_tail_bytes(codec, S, kind):
         assert np.array_equal(G.gpu_decompress(codec, got), x)
         with pytest.raises(lz.LzError):
             codec.compress(d, lz.Params(*P.tuple()))
+
+
+OVERLAP_GRID = [(1, 4096, 128, 3, 255), (2, 4096, 128, 3, 255), (4, 8192, 256, 2, 255),
+                (1, 64, 33, 1, 1), (2, 16, 1, 1, 1), (4, 32, 7, 2, 3), (1, 512, 100, 4, 40),
+                (2, 1024, 1024, 3, 255), (4, 2048, 32, 1, 255), (1, 16384, 512, 3, 255)]
+
+
+@pytest.mark.parametrize("S,C,W,m,M", OVERLAP_GRID)
+@pytest.mark.parametrize("kind", KINDS)
+def test_v2_overlap_mode(codec, S, C, W, m, M, kind):
+    """LZ_MATCH_OVERLAP (pointers may be longer than their offset): streams
+    byte-identical to the oracle's MATCH_OVERLAP streams, decoded exactly."""
+    P = Params(S, C, W, m, M)
+    n_sym = (4 * C + C // 2) // S
+    check(codec, make_input(kind, n_sym, S, seed=S * 13 + W), P, match=lz.LZ_MATCH_OVERLAP)
+
+
+def test_v2_overlap_needs_version2_and_flag(codec):
+    d = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    out = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(lz.LzError):
+        lz.lz_compress_ex(codec.ctx, d.data_ptr(), 64, lz.Params(1, 64, 8, 2, 255),
+                          out.data_ptr(), out.numel(), nb.data_ptr(),
+                          torch.cuda.current_stream().cuda_stream, match=lz.LZ_MATCH_OVERLAP,
+                          version=1)
+    x = np.full(5000, 9, np.uint8)
+    s = oracle.compress(x, Params(1, 4096, 64, 3, 255), mode=oracle.MATCH_OVERLAP, version=2)
+    assert np.array_equal(G.gpu_decompress(codec, s), x)
+    bad = s.copy()
+    bad[9] = 0  # pointers longer than their offset without the flag: corrupt
+    with pytest.raises(lz.LzError):
+        G.gpu_decompress(codec, bad)

@@ -591,3 +591,71 @@ def test_v2_tail_bytes(S):
             rec = s.tobytes()[at + (ntok + 7) // 8: at + (ntok + 7) // 8 + pay]
             assert rec[-tail:] == x.tobytes()[n - tail:]
             assert sum(l for l, _ in st.tokens[-1]) == k
+
+
+# --- stream version 2: overlap-allowed mode ---------------------------------------
+
+def brute_longest_overlap(sym: list, p: int, W: int, M: int):
+    """Longest match when it may run into the look-ahead: for each offset the
+    longest l <= min(M, k - p) with equal slices (slices of the input may
+    overlap), longest first; nearest offset on ties."""
+    k = len(sym)
+    best, best_d = 0, 0
+    for d in range(1, min(W, p) + 1):
+        for l in range(min(M, k - p), 0, -1):
+            if sym[p:p + l] == sym[p - d:p - d + l]:
+                break
+        else:
+            l = 0
+        if l > best:
+            best, best_d = l, d
+    return best, best_d
+
+
+@pytest.mark.parametrize("alpha", [1, 2, 3])
+def test_overlap_match_exhaustive_tiny(alpha):
+    for n in range(1, 8):
+        for seq in itertools.product(range(alpha), repeat=n):
+            b = bytes(seq)
+            sym = symbols(b, 1)
+            for W, M in ((1, 255), (2, 3), (3, 2), (8, 255)):
+                for p in range(n):
+                    assert oracle.longest_match_overlap(b, p, 1, W, M) == \
+                        brute_longest_overlap(sym, p, W, M)
+
+
+def test_overlap_closed_forms():
+    """A constant run is one literal and then pointers at offset 1 of length
+    min(M, symbols left); x[i] = i mod q takes offset q with the longest
+    length the chunk and M allow."""
+    k, M = 1000, 255
+    toks = oracle.parse_chunk(np.full(k, 5, np.uint8).tobytes(), 1, 64, 3, M, mode=oracle.MATCH_OVERLAP)
+    want, p = [(1, 0)], 1
+    while p < k:
+        l = min(M, k - p)
+        want.append((l, 1) if l >= 3 else (1, 0))
+        p += l if l >= 3 else 1
+    assert toks == want
+    for q in (2, 5, 17):
+        x = (np.arange(600) % q).astype(np.uint8).tobytes()
+        for p in range(q, 600, 37):
+            assert oracle.longest_match_overlap(x, p, 1, 64, 255) == (min(255, 600 - p), q)
+
+
+@pytest.mark.parametrize("S", [1, 2, 4])
+def test_overlap_round_trip_and_flag(S):
+    rng = np.random.default_rng(S + 50)
+    x = np.repeat(rng.integers(0, 4, 3000), rng.integers(1, 30, 3000))[: 12000 // S * S]
+    x = x.astype({1: np.uint8, 2: np.uint16, 4: np.uint32}[S])
+    P = Params(S, 4096, 128, 2, 255)
+    with pytest.raises(oracle.OracleError):
+        oracle.compress(x, P, mode=oracle.MATCH_OVERLAP)  # version 1 has no overlaps
+    s = oracle.compress(x, P, mode=oracle.MATCH_OVERLAP, version=2)
+    assert s[9] == 1 and np.array_equal(oracle.decompress(s), x.view(np.uint8))
+    st = glz1_reader.read(s.tobytes())
+    assert st.overlap and any(l > d for t in st.tokens for l, d in t if d)
+    assert s.size < oracle.compress(x, P, version=2).size
+    bad = bytearray(s.tobytes()); bad[9] = 0   # pointers longer than their offset, no flag
+    assert oracle.decompress_status(bytes(bad)) == oracle.ECORRUPT
+    bad = bytearray(s.tobytes()); bad[9] = 2
+    assert oracle.decompress_status(bytes(bad)) == oracle.ECORRUPT
