@@ -344,6 +344,8 @@ def run_gpu(args):
         line["paper_matcher"] = _paper_matcher(torch, codec, args)
     if args.huffman:
         line["huffman"] = _huffman(torch, codec, args)
+    if args.sweep:
+        line["sweep"] = _sweep(torch, codec, args)
     if args.batched:
         line["batched"] = _batched(torch, codec, args)
     if args.served > 0:
@@ -438,6 +440,58 @@ def _huffman(torch, codec, args, n_sym: int = 128 << 20, reps: int = 5):
     del d, s1, h2
     torch.cuda.empty_cache()
     return out
+
+
+def _sweep(torch, codec, args, reps: int = 3):
+    """The symbol-size sweep workload: 1 GiB of first-order Markov codes
+    stored as uint8, uint16 and uint32 (S = 1, 2, 4), compressed with chunk
+    2-16 KiB x window 64-512 symbols (m = 3 for S = 1, 2 and 2 for S = 4),
+    and 1 GiB of uniform random bytes as the control.  Per point: compress
+    and decompress GB/s (CUDA events, `reps` calls after a checked one) and
+    the ratio."""
+    from paper_2304_07342_gb300 import lz, synth
+    st = torch.cuda.current_stream()
+    chain = synth.markov_codes(1 << 30, seed=args.seed)
+    rows = []
+    inputs = [(f"markov u{8 * S}", S, ((chain % 256).astype(np.uint8) if S == 1 else
+                                       chain[: (1 << 30) // S].astype({2: np.uint16, 4: np.uint32}[S])))
+              for S in (1, 2, 4)]
+    del chain
+    inputs.append(("uniform bytes", 1, synth.uniform_bytes(1 << 30, seed=args.seed + 7)))
+    for name, S, x in inputs:
+        d = torch.from_numpy(np.ascontiguousarray(x).view(np.uint8)).cuda()
+        n = d.numel()
+        grid = [(C, W) for C in (2048, 4096, 8192, 16384) for W in (64, 128, 256, 512)]
+        if name == "uniform bytes":
+            grid = [(8192, 256)]
+        for C, W in grid:
+            P = lz.Params(S, C, W, 2 if S == 4 else 3, 255)
+            out, nb = codec.compress(d, P)
+            back, bb = codec.decompress(out, n_bytes=n)
+            if codec.sync() != lz.LZ_OK:
+                raise RuntimeError("sweep point failed on the device")
+            size = int(nb.item())
+            if not torch.equal(back, d):
+                raise RuntimeError(f"sweep round trip differs: {name} C={C} W={W}")
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(st)
+            for _ in range(reps):
+                codec.compress(d, P, out=out, out_bytes=nb)
+            ev[1].record(st)
+            for _ in range(reps):
+                codec.decompress(out, n_bytes=n, out=back, out_bytes=bb, in_bytes=size)
+            ev[2].record(st)
+            torch.cuda.synchronize()
+            c_ms = ev[0].elapsed_time(ev[1]) / reps
+            d_ms = ev[1].elapsed_time(ev[2]) / reps
+            rows.append({"input": name, "S": S, "C": C, "W": W, "ratio": round(n / size, 4),
+                         "compress_gbs": round(n / (c_ms * 1e-3) / 1e9, 2),
+                         "decompress_gbs": round(n / (d_ms * 1e-3) / 1e9, 2)})
+            del out, back
+        del d
+        torch.cuda.empty_cache()
+    return {"workload": "1 GiB Markov codes as uint8/uint16/uint32 + 1 GiB uniform bytes",
+            "points": rows}
 
 
 def _batched(torch, codec, args, n_buffers: int = 10_000):
@@ -642,6 +696,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-version2", dest="version2", action="store_false",
                     help="skip the stream-version-2 (stored chunks) pass")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also run the 1 GiB symbol-size sweep (S x chunk x window)")
     ap.add_argument("--no-huffman", dest="huffman", action="store_false",
                     help="skip the LZSS-then-Huffman use case")
     ap.add_argument("--no-paper-matcher", dest="paper_matcher", action="store_false",

@@ -235,6 +235,15 @@ typedef struct lz_batch lz_batch;
 lz_status lz_batch_create(lz_ctx *ctx, const lz_batch_item *items, uint32_t n_items,
                           int decompress, lz_stream_t stream, lz_batch **out);
 
+/* lz_batch_create with options for a compression batch: every item is
+ * compressed with opt->match and written as stream version opt->version,
+ * exactly as lz_compress_ex with the same options would (opt NULL: the
+ * defaults; ignored for a decompression batch, which reads both versions).
+ * LZ_ERR_INVALID_ARG for the combinations lz_compress_ex rejects. */
+lz_status lz_batch_create_ex(lz_ctx *ctx, const lz_batch_item *items, uint32_t n_items,
+                             int decompress, const lz_options *opt, lz_stream_t stream,
+                             lz_batch **out);
+
 /* Enqueue one run of the batch on `stream`. */
 lz_status lz_batch_run(lz_ctx *ctx, lz_batch *batch, lz_stream_t stream);
 

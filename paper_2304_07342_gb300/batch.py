@@ -53,12 +53,23 @@ def make_pools(torch, pool_bytes: int = 256 << 20, seed: int = 0, device="cuda")
 
 def autotuned_params(codec, pools, sample_bytes: int = 8 << 20) -> list:
     """Chunk size and window per kind from ``lz_autotune`` on the head of
-    each kind's pool."""
-    out = []
+    each kind's pool.  One launch sizes every warp's shared memory for the
+    largest chunk of the batch, so a kind whose sample does not compress
+    (where a large chunk only saves per-chunk overhead) is held to the
+    largest chunk chosen for a kind that does compress."""
+    out, ratios = [], []
     for k, pool in enumerate(pools):
         n = min(pool.numel(), sample_bytes)
         n -= n % KIND_S[k]
-        out.append(lz.lz_autotune(codec.ctx, pool.data_ptr(), n, KIND_S[k]))
+        p = lz.lz_autotune(codec.ctx, pool.data_ptr(), n, KIND_S[k])
+        s = codec.compress_sync(pool[:n], p)
+        out.append(p)
+        ratios.append(n / max(1, s.numel()))
+    caps = [p.C for p, r in zip(out, ratios) if r >= 1.05]
+    if caps:
+        cap = max(caps)
+        out = [p if r >= 1.05 or p.C <= cap else lz.Params(p.S, cap, p.W, p.m, p.M)
+               for p, r in zip(out, ratios)]
     return out
 
 

@@ -111,7 +111,7 @@ __device__ __forceinline__ void key_at(const uint8_t *in, uint32_t p, uint32_t m
 // slabs need the lane groups of __match_any_sync (a shared unit with low
 // throughput).  The key filter runs after four slabs have been linked, on
 // independent loads.
-constexpr uint32_t kFilterHops = 4;  // chain entries the candidate filter inspects
+constexpr uint32_t kFilterHops = 2;  // chain entries the candidate filter inspects
 
 template <int S, bool WIDE>
 __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,

@@ -289,7 +289,7 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
         const uint32_t o_off = __shfl_sync(kFull, off, lo);
         const uint32_t o_val = __shfl_sync(kFull, val, lo);
         uint32_t f = (active && o_ism) ? jp - o_off : jp;
-        // resolve sources inside this round by pointer jumping
+        // resolve sources inside these 32 positions by pointer jumping
 #pragma unroll
         for (int it = 0; it < 5; ++it) {
           const uint32_t src_lane = f >= r0 ? f - r0 : lane;

@@ -691,7 +691,7 @@ glz::CompressSmem compress_layout_max(const std::vector<lz_params> &ps) {
 }
 
 lz_status batch_create_compress(lz_ctx *ctx, const lz_batch_item *items, uint32_t n,
-                                lz_batch *b) {
+                                lz_batch *b, uint32_t match, uint32_t version) {
   std::vector<glz::BufDesc> descs, empties;
   std::vector<uint64_t> bases;
   std::vector<lz_params> ps;
@@ -703,7 +703,7 @@ lz_status batch_create_compress(lz_ctx *ctx, const lz_batch_item *items, uint32_
     if (!params_ok(p) || !it.d_out || !it.d_out_bytes) return LZ_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(it.d_out_bytes) % 8 != 0) return LZ_ERR_INVALID_ARG;
     if (it.in_bytes > 0 && !it.d_in) return LZ_ERR_INVALID_ARG;
-    if (it.in_bytes % p->symbol_bytes != 0) return LZ_ERR_INVALID_ARG;
+    if (version == 1 && it.in_bytes % p->symbol_bytes != 0) return LZ_ERR_INVALID_ARG;
     const uint64_t nc = div_up(it.in_bytes, p->chunk_bytes);
     if (nc > 0xFFFFFFFFull) return LZ_ERR_INVALID_ARG;
     const uint64_t records_at = glz::kHeaderBytes + glz::kTableEntry * nc +
@@ -725,6 +725,8 @@ lz_status batch_create_compress(lz_ctx *ctx, const lz_batch_item *items, uint32_
     d.in_aligned = (reinterpret_cast<uintptr_t>(it.d_in) % 16) == 0;
     d.records_at = records_at;
     d.gbase = total;
+    d.match = match;
+    d.version = version;
     if (nc == 0) {
       empties.push_back(d);
       continue;
@@ -893,7 +895,19 @@ extern "C" {
 
 lz_status lz_batch_create(lz_ctx *ctx, const lz_batch_item *items, uint32_t n_items,
                           int decompress, lz_stream_t stream, lz_batch **out) {
+  return lz_batch_create_ex(ctx, items, n_items, decompress, nullptr, stream, out);
+}
+
+lz_status lz_batch_create_ex(lz_ctx *ctx, const lz_batch_item *items, uint32_t n_items,
+                             int decompress, const lz_options *opt, lz_stream_t stream,
+                             lz_batch **out) {
   if (!ctx || !out || (n_items > 0 && !items)) return LZ_ERR_INVALID_ARG;
+  const uint32_t match = opt ? opt->match : LZ_MATCH_EXACT;
+  const uint32_t version = opt && opt->version ? opt->version : 1u;
+  if (match != LZ_MATCH_EXACT && match != LZ_MATCH_PAPER && match != LZ_MATCH_OVERLAP)
+    return LZ_ERR_INVALID_ARG;
+  if ((version != 1 && version != 2) || (match == LZ_MATCH_OVERLAP && version != 2))
+    return LZ_ERR_INVALID_ARG;
   *out = nullptr;
   std::lock_guard<std::mutex> lock(ctx->mu);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
@@ -902,8 +916,11 @@ lz_status lz_batch_create(lz_ctx *ctx, const lz_batch_item *items, uint32_t n_it
   b->decompress = decompress ? 1 : 0;
   b->device = ctx->device;
   b->stream = reinterpret_cast<cudaStream_t>(stream);
+  const uint32_t kmatch = match == LZ_MATCH_PAPER     ? glz::kMatchPaper
+                         : match == LZ_MATCH_OVERLAP ? glz::kMatchOverlap
+                                                     : glz::kMatchExact;
   lz_status s = decompress ? batch_create_decompress(ctx, items, n_items, b)
-                           : batch_create_compress(ctx, items, n_items, b);
+                           : batch_create_compress(ctx, items, n_items, b, kmatch, version);
   if (s != LZ_OK) {
     for (void *p : b->owned) cudaFreeAsync(p, b->stream);
     delete b;

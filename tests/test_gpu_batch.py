@@ -143,3 +143,37 @@ def test_autotune_picks_valid_exact_params(codec):
     small = x[: 20_000]
     got = G.gpu_compress(codec, small, P)
     assert np.array_equal(got, oracle.compress(small, oracle.Params(P.S, P.C, P.W, P.m, P.M)))
+
+
+@pytest.mark.parametrize("match,version", [(lz.LZ_MATCH_EXACT, 2), (lz.LZ_MATCH_PAPER, 1),
+                                           (lz.LZ_MATCH_PAPER, 2), (lz.LZ_MATCH_OVERLAP, 2)])
+def test_batch_options_equal_single_calls(codec, match, version):
+    """lz_batch_create_ex: every item equals lz_compress_ex with the same
+    matcher and stream version (and the oracle for the small ones); the
+    streams decode through a batched decompression."""
+    items = _items(seed=5, n=24)
+    ins, outs, nbs, desc = [], [], [], []
+    for x, P in items:
+        d = G.to_dev(x) if x.nbytes else torch.empty(16, dtype=torch.uint8, device="cuda")[:0]
+        cap = lz.lz_compressed_bound(x.nbytes, P)
+        o = torch.full((cap,), 0x5A, dtype=torch.uint8, device="cuda")
+        nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+        ins.append(d); outs.append(o); nbs.append(nb)
+        desc.append((d.data_ptr() if x.nbytes else 0, x.nbytes, o.data_ptr(), cap, nb.data_ptr(), P))
+    st = torch.cuda.current_stream().cuda_stream
+    b = lz.lz_batch_create(codec.ctx, desc, stream=st, match=match, version=version)
+    lz.lz_batch_run(codec.ctx, b, st)
+    lz.lz_batch_destroy(b, st)
+    assert codec.sync() == lz.LZ_OK
+    for (x, P), d, o, nb in zip(items, ins, outs, nbs):
+        got = o[: int(nb.item())].cpu().numpy()
+        if x.nbytes <= 64 * 1024:
+            ref = oracle.compress(x, oracle.Params(P.S, P.C, P.W, P.m, P.M), mode=match,
+                                  version=version)
+        else:
+            ref = codec.compress_sync(d, P, match=match, version=version).cpu().numpy()
+        assert np.array_equal(got, ref), (P, x.nbytes, G.first_difference(got, ref))
+        if x.nbytes:
+            assert np.array_equal(G.gpu_decompress(codec, got), x.view(np.uint8).reshape(-1))
+    with pytest.raises(lz.LzError):
+        lz.lz_batch_create(codec.ctx, desc, stream=st, match=lz.LZ_MATCH_OVERLAP, version=1)
