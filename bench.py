@@ -590,41 +590,19 @@ def _e2e(codec, items, stream, args):
     steps = max(1, min(args.steps, 5))
     streams = [stream] + [torch.cuda.Stream() for _ in items[1:]]
     codecs = [codec] + [lz.Codec(codec.device) for _ in items[1:]]
-    # each copy is split into pieces on helper streams, so that several copy
-    # engines move one item at once
-    pieces = 4
-    helpers = [[torch.cuda.Stream() for _ in range(pieces)] for _ in items]
-
-    def split_copy(dst, src, st, hs):
-        n = dst.numel()
-        step = (n + pieces - 1) // pieces
-        ready = torch.cuda.Event()
-        ready.record(st)
-        evs = []
-        for j, h in enumerate(hs):
-            lo, hi_ = j * step, min(n, (j + 1) * step)
-            if lo >= hi_:
-                continue
-            h.wait_event(ready)
-            with torch.cuda.stream(h):
-                dst[lo:hi_].copy_(src[lo:hi_], non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(h)
-            evs.append(ev)
-        for ev in evs:
-            st.wait_event(ev)
-
     def one():
         start = torch.cuda.Event()
         start.record(stream)
         done = []
-        for it, hi, ho, st, cd, hs in zip(items, pinned_in, pinned_out, streams, codecs, helpers):
+        for it, hi, ho, st, cd in zip(items, pinned_in, pinned_out, streams, codecs):
             st.wait_event(start)
-            split_copy(it["d_in"], hi, st, hs)
+            with torch.cuda.stream(st):
+                it["d_in"].copy_(hi, non_blocking=True)
             lz.lz_compress(cd.ctx, it["d_in"].data_ptr(), it["d_in"].numel(), it["p"],
                            it["d_out"].data_ptr(), it["cap"], it["d_nb"].data_ptr(),
                            st.cuda_stream)
-            split_copy(ho[: it["size"]], it["d_out"][: it["size"]], st, hs)
+            with torch.cuda.stream(st):
+                ho[: it["size"]].copy_(it["d_out"][: it["size"]], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
             done.append(ev)
@@ -655,9 +633,8 @@ def _e2e(codec, items, stream, args):
     return {"value": round(n_in / (ms * 1e-3) / 1e9, 3), "unit": "GB/s",
             "h2d_bytes_per_step": int(n_in),
             "d2h_bytes_per_step": int(sum(it["size"] for it in items)),
-            "note": "one stream and context per item, each copy split over 4 streams; the "
-                    "stream size is known from the warm-up pass and D2H copies exactly that "
-                    "many bytes"}
+            "note": "one stream and context per item; the stream size is known from the "
+                    "warm-up pass and D2H copies exactly that many bytes"}
 
 
 def _cpu_baseline(args, budget_s: float = 15.0, hosts=None):

@@ -6,26 +6,30 @@
 // takes the next chunk from a work counter and
 //   1. stages the chunk into its shared-memory slice (1-D TMA bulk copy);
 //   2. checks whether any position can start a match at all (a Bloom
-//      filter over symbol keys; chunks without repeats end here as all
-//      literals), else
-//      links every position to the last earlier position with the same
-//      hash of its first min(m, 8/S) symbols (hash chains; __match_any_sync
-//      links positions of one 32-position slab) and marks the positions
-//      whose chain reaches into the window -- only those can start a match
-//      of >= m symbols;
+//      filter over symbol keys, tried after a chunk without pointers;
+//      chunks without repeats end here as all literals), else links every
+//      position to the last earlier position with the same hash of its
+//      first min(m, 8/S) symbols (hash chains; __match_any_sync links
+//      positions of one 32-position slab) and marks the positions whose
+//      chain holds their key inside the window -- only those can start a
+//      match of >= m symbols;
 //   3. walks the greedy parse (section 2.2 steps 1-6): the next 32 marked
 //      positions are evaluated in parallel, one lane each, by walking their
 //      chains nearest-first and extending every candidate exactly (length
-//      <= offset, section 3.3.2) -- or, in the paper's matcher mode, by
-//      the paper's forward scan of the window -- the parse through the batch is found by a
-//      short chase over lanes, then warp scans give each token its index
-//      and payload offset (the local, first pass of the two-pass prefix sum
-//      of section 3.2.2) and the lanes write the tokens in parallel into a
-//      staging record in shared memory;
-//   4. obtains its record's global offset from a decoupled look-back over
+//      <= offset, section 3.3.2; not bounded by the offset in the overlap
+//      mode of stream version 2) or, with the paper's matcher, by the
+//      paper's forward scan of the window.  The parse through the batch is
+//      found by a short chase over lanes, then warp scans give each token
+//      its index and payload offset (the local, first pass of the two-pass
+//      prefix sum of section 3.2.2) and the lanes write the tokens in
+//      parallel into a staging record in shared memory;
+//   4. in stream version 2, appends the bytes after the last whole symbol
+//      and stores the chunk as it is if its record would not be smaller;
+//   5. obtains its record's global offset from a decoupled look-back over
 //      the chunks before it (the second pass) -- bounded spins, no extra
-//      kernel, no per-symbol data in HBM;
-//   5. writes its table entry, index entry and record at the final offset.
+//      kernel, no per-symbol data in HBM -- or parks the record (by
+//      reference when it is the chunk's own input) and moves on;
+//   6. writes its table entry, index entry and record at the final offset.
 #pragma once
 
 #include <cstdint>
@@ -109,9 +113,9 @@ __device__ __forceinline__ void key_at(const uint8_t *in, uint32_t p, uint32_t m
 // their position and read it back; a lane that finds another position lost
 // a collision, so its slab holds two positions with one hash.  Only such
 // slabs need the lane groups of __match_any_sync (a shared unit with low
-// throughput).  The key filter runs after four slabs have been linked, on
+// throughput).  The key filter runs after kGroup slabs have been linked, on
 // independent loads.
-constexpr uint32_t kFilterHops = 2;  // chain entries the candidate filter inspects
+constexpr uint32_t kFilterHops = 1;  // chain entries the candidate filter inspects
 
 template <int S, bool WIDE>
 __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
@@ -131,7 +135,7 @@ __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
   const uint32_t tshift = 32u - sm.hash_log2;
   const uint32_t lt = lanemask_lt(lane);
   const uint32_t nslab = (k + 31) / 32;
-  constexpr uint32_t kGroup = 4;  // slabs whose hashes and filters are formed together
+  constexpr uint32_t kGroup = 2;  // slabs whose hashes and filters are formed together
   for (uint32_t s0 = 0; s0 < nslab; s0 += kGroup) {
     uint32_t hh[kGroup], klo[kGroup], khi[kGroup], qq[kGroup], dd[kGroup];
     bool okk[kGroup];
@@ -712,7 +716,7 @@ __device__ __forceinline__ void greedy_walk(const typename SymType<S>::T *sym,
   pay_out = pb;
 }
 
-// Step 4: decoupled look-back (single-pass scan over chunks).  Status word:
+// Step 5: decoupled look-back (single-pass scan over chunks).  Status word:
 // bit 63 = inclusive prefix, bit 62 = aggregate only, low bits = value;
 // 0 = not published yet.
 constexpr unsigned long long kPrefix = 1ull << 63, kAgg = 1ull << 62;
@@ -783,7 +787,7 @@ __device__ __forceinline__ void warp_zero(uint8_t *dst, uint32_t n, uint32_t lan
   if (lane < n - done) dst[done + lane] = 0;
 }
 
-// Step 5 for a chunk whose global offset is known: publish its inclusive
+// Step 6 for a chunk whose global offset is known: publish its inclusive
 // prefix, its index entry (every 64th chunk), the stream size (last chunk)
 // and copy its record (from shared staging or a parking slot; src1 ==
 // nullptr writes n1 zero bytes).
@@ -906,7 +910,7 @@ __device__ __forceinline__ void write_header(const BufDesc &B, uint32_t lane) {
   B.out[lane] = static_cast<uint8_t>(b);
 }
 
-// Steps 1-5 for chunk c of buffer B (item `item` of a batch).  Returns false
+// Steps 1-6 for chunk c of buffer B (item `item` of a batch).  Returns false
 // when the TMA copy never landed (the warp must stop: its barrier phase is
 // unknown; the chunk was still published so no other warp waits on it).
 template <int S, int NJ, bool WIDE>
@@ -977,7 +981,7 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
   }
   if (!sane && lane == 0) atomicOr(A.err, kErrInternal);
   W.try_literal = payload == W.inb;  // no pointer in this chunk
-  // stream version 2, last chunk: the 1..S-1 bytes after the last whole
+  // 4. stream version 2, last chunk: the 1..S-1 bytes after the last whole
   // symbol follow the tokens as they are (in the staged chunk they already
   // follow the k symbols)
   const uint32_t tail = bytes - k * S;
@@ -997,7 +1001,7 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
   }
   const uint64_t rec = static_cast<uint64_t>(fb) + pb;
 
-  // 4. global offset: publish the aggregate at once, so that no other
+  // 5. global offset: publish the aggregate at once, so that no other
   // chunk waits on this warp; place the record now if the offset is
   // known, else park it and move on (placed after a later chunk)
   const bool data_ok = staged && sane;
