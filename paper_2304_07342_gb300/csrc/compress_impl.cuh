@@ -217,10 +217,13 @@ __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
 // returns true for a chunk with a match, and on data without repeats it
 // returns true after one shared-memory atomic per position.
 //
-// Every position with room for m symbols ORs a 3-bit mask, drawn from a hash
+// Every position with room for m symbols ORs a 4-bit mask, drawn from a hash
 // of its key (its first g symbols, as for the chains), into one 32-bit word
 // of a bitmap that starts empty (a blocked Bloom filter over the keys seen
-// so far in the chunk).  The atomic returns the word before the OR; a
+// so far in the chunk; the word is the high half of hash x word count, so
+// the bitmap fills whatever shared memory the chains would use, about 10
+// bits per position for 4-byte symbols).  The atomic returns the word before
+// the OR; a
 // position finds all its bits already set ("flagged") whenever an earlier
 // position of an earlier slab has its key.  Two positions of one slab that
 // share a key are ordered by the atomic unit, not by position, so it is the
@@ -239,18 +242,32 @@ constexpr uint32_t kBloomGroup = 8;  // slabs whose ORs are issued together
 // Does p (flagged, p + m <= k) take part in a match of >= m symbols, as the
 // position coded ((i)) or as the source of a later position of its slab
 // that ends at `slab_end` ((ii))?  Warp-wide; every lane returns the answer.
+// (i) takes four offsets per lane per round: their first symbols are loaded
+// before any is compared, so the loads overlap.
 template <int S>
 __device__ __forceinline__ bool match_near(const typename SymType<S>::T *sym, uint32_t k,
                                            const BufDesc &A, uint32_t p, uint32_t slab_end,
                                            uint32_t lane) {
+  using Sym = typename SymType<S>::T;
   const uint32_t dmax = min(A.W, p);
+  // a match of >= m symbols needs offset >= m unless matches may overlap
+  const uint32_t dmin = A.match == kMatchOverlap ? 1u : A.m;
+  const Sym first = sym[p];
   bool hit = false;
-  for (uint32_t d0 = 0; d0 < dmax; d0 += 32) {
-    const uint32_t d = d0 + lane + 1;
-    // a match of >= m symbols needs offset >= m unless matches may overlap
-    bool eq = (d >= A.m || A.match == kMatchOverlap) && d <= dmax;
-    for (uint32_t i = 0; eq && i < A.m; ++i) eq = sym[p + i] == sym[p - d + i];
-    hit |= eq;
+  for (uint32_t d0 = 0; d0 < dmax; d0 += 128) {
+    Sym v[4];
+#pragma unroll
+    for (uint32_t u = 0; u < 4; ++u) {
+      const uint32_t d = d0 + 32 * u + lane + 1;
+      v[u] = d <= dmax ? sym[p - d] : first;
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < 4; ++u) {
+      const uint32_t d = d0 + 32 * u + lane + 1;
+      bool eq = v[u] == first && d >= dmin && d <= dmax;
+      for (uint32_t i = 1; eq && i < A.m; ++i) eq = sym[p + i] == sym[p - d + i];
+      hit |= eq;
+    }
   }
   const uint32_t q = p + 1 + lane;
   bool eq = q < slab_end && (q - p >= A.m || A.match == kMatchOverlap) && q - p <= A.W &&
@@ -260,18 +277,18 @@ __device__ __forceinline__ bool match_near(const typename SymType<S>::T *sym, ui
   return __any_sync(kFull, hit);
 }
 
+// `bm` holds `nwords` words (a multiple of 4, 16-byte aligned).
 template <int S>
 __device__ __forceinline__ bool literal_chunk(const typename SymType<S>::T *sym, uint32_t k,
-                                              const BufDesc &A, uint32_t *bm, uint32_t bl,
+                                              const BufDesc &A, uint32_t *bm, uint32_t nwords,
                                               uint32_t *maybe, uint32_t lane) {
   uint4 *b4 = reinterpret_cast<uint4 *>(bm);
-  for (uint32_t i = lane; i < (1u << bl) / 4; i += 32) b4[i] = make_uint4(0, 0, 0, 0);
+  for (uint32_t i = lane; i < nwords / 4; i += 32) b4[i] = make_uint4(0, 0, 0, 0);
   __syncwarp();
   const uint8_t *in = reinterpret_cast<const uint8_t *>(sym);
   const uint32_t kb = S * min(A.m, 8u / S);  // key bytes, as in build_chains
   const uint32_t mlo = kb >= 4 ? kFull : (1u << (8 * kb)) - 1u;
   const uint32_t mhi = kb <= 4 ? 0u : (kb >= 8 ? kFull : (1u << (8 * (kb - 4))) - 1u);
-  const uint32_t wshift = 32u - bl;
   const uint32_t nslab = (k + 31) / 32;
   uint32_t nflag = 0;
   // groups of kBloomGroup slabs: keys and masks first, then the ORs in slab
@@ -288,8 +305,9 @@ __device__ __forceinline__ bool literal_chunk(const typename SymType<S>::T *sym,
       if (ok) key_at<S>(in, p, mlo, mhi, lo, hi);
       const uint32_t h = ((hi * 0x85EBCA77u) ^ lo) * 0x9E3779B1u;
       const uint32_t g = h * 0xC2B2AE3Du;
-      widx[u] = h >> wshift;
-      mask[u] = (1u << (g >> 27)) | (1u << ((g >> 22) & 31u)) | (1u << ((g >> 17) & 31u));
+      widx[u] = __umulhi(h, nwords);
+      mask[u] = (1u << (g >> 27)) | (1u << ((g >> 22) & 31u)) | (1u << ((g >> 17) & 31u)) |
+                (1u << ((g >> 12) & 31u));
       okk[u] = ok;
     }
 #pragma unroll
@@ -948,17 +966,18 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
   }
   __syncwarp();
 
-  // 2. literal pre-check (when the payload area holds a bitmap of >= 16
-  // bits per position), else the candidate filter (hash table in the
-  // payload staging area)
+  // 2. literal pre-check (when the payload area alone could hold a bitmap
+  // of >= 16 bits per position; the bitmap itself spans the links, flags
+  // and payload areas, contiguous and unused until the chains), else the
+  // candidate filter (hash table in the payload staging area)
   const uint32_t bl = 31u - __clz(A.sm.pay_bytes / 4);  // bitmap words = 2^bl
   bool literal = false;
   // (tried when this warp's previous chunk was all literals: on data with
   // repeats the check would only give up, so it is not tried again until a
   // chunk without a match comes by)
   if (W.try_literal && bl >= 2 && (2u << bl) >= k)
-    literal = literal_chunk<S>(sym, k, B, reinterpret_cast<uint32_t *>(W.pay), bl, W.maybe,
-                               lane);
+    literal = literal_chunk<S>(sym, k, B, reinterpret_cast<uint32_t *>(W.links_base),
+                               (A.sm.maybe_off - A.sm.prev_off) / 4, W.maybe, lane);
   uint32_t marked = 0;
   if (!literal) {
     build_chains<S, WIDE>(sym, k, B, A.sm, reinterpret_cast<uint16_t *>(W.pay), W.maybe,
