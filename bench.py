@@ -19,7 +19,7 @@ After the timed steps (not part of them) the line gets more sections on
 the same GPU: `stream_version2` -- the same items as stream version 2
 (stored chunks); `paper_matcher` -- the paper's own matcher (section 3.3.2)
 beside the exact one on 256 MiB of uint16 quantization codes; `huffman` --
-the paper's use case (section 4.4), Huffman coding after LZSS, on the same
+the paper's use case (section 4.5), Huffman coding after LZSS, on the same
 codes; `batched` --
 10,000 uneven buffers (4 KiB-16 MiB, four
 kinds, about 20 GB) compressed and decompressed by one persistent launch
@@ -385,7 +385,7 @@ def _paper_matcher(torch, codec, args, n_sym: int = 128 << 20):
 
 
 def _huffman(torch, codec, args, n_sym: int = 128 << 20, reps: int = 5):
-    """The paper's use case (section 4.4): Huffman coding after LZSS, on 256
+    """The paper's use case (section 4.5): Huffman coding after LZSS, on 256
     MiB of uint16 quantization codes.  Ratios of Huffman alone, LZSS alone
     and LZSS then Huffman; GB/s of the Huffman encoder (input bytes) and
     decoder (output bytes), CUDA events over `reps` calls."""
@@ -630,11 +630,57 @@ def _e2e(codec, items, stream, args):
             cd.close()
     ms = a.elapsed_time(b) / steps
     n_in = sum(it["d_in"].numel() for it in items)
+    n_out = sum(it["size"] for it in items)
     return {"value": round(n_in / (ms * 1e-3) / 1e9, 3), "unit": "GB/s",
             "h2d_bytes_per_step": int(n_in),
-            "d2h_bytes_per_step": int(sum(it["size"] for it in items)),
+            "d2h_bytes_per_step": int(n_out),
+            "link": _link_bandwidth(items, pinned_in, pinned_out, streams),
             "note": "one stream and context per item; the stream size is known from the "
                     "warm-up pass and D2H copies exactly that many bytes"}
+
+
+def _link_bandwidth(items, pinned_in, pinned_out, streams):
+    """Host-link bandwidth on the end-to-end pass's own pinned buffers:
+    all inputs host to device, all streams device to host, and both at once
+    on two streams (CUDA events, best of 3 after one warm-up)."""
+    import torch
+
+    n_in = sum(it["d_in"].numel() for it in items)
+    n_out = sum(it["size"] for it in items)
+    s_in, s_out = streams[0], (streams[1] if len(streams) > 1 else torch.cuda.Stream())
+
+    def h2d():
+        for it, hi in zip(items, pinned_in):
+            with torch.cuda.stream(s_in):
+                it["d_in"].copy_(hi, non_blocking=True)
+
+    def d2h():
+        for it, ho in zip(items, pinned_out):
+            with torch.cuda.stream(s_out):
+                ho[: it["size"]].copy_(it["d_out"][: it["size"]], non_blocking=True)
+
+    def timed(fn):
+        best = float("inf")
+        for rep in range(4):
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(s_in)
+            s_out.wait_stream(s_in)
+            fn()
+            s_in.wait_stream(s_out)
+            b.record(s_in)
+            torch.cuda.synchronize()
+            if rep:
+                best = min(best, a.elapsed_time(b))
+        return best
+
+    t_in, t_out = timed(h2d), timed(d2h)
+    t_both = timed(lambda: (h2d(), d2h()))
+    return {"h2d_gbs": round(n_in / (t_in * 1e-3) / 1e9, 1),
+            "d2h_gbs": round(n_out / (t_out * 1e-3) / 1e9, 1),
+            "both_gbs": round((n_in + n_out) / (t_both * 1e-3) / 1e9, 1),
+            "note": "pinned copies of the same buffers, no compression"}
 
 
 def _cpu_baseline(args, budget_s: float = 15.0, hosts=None):

@@ -315,7 +315,7 @@ lz_status lz_stitch(lz_ctx *ctx, const void *d_shard, uint64_t shard_bytes,
 lz_status lz_sync(lz_ctx *ctx, lz_stream_t stream);
 
 /* ---- Huffman stage ----------------------------------------------------------
- * In the paper's use case (section 4.4) gpuLZ runs before cuSZ's Huffman
+ * In the paper's use case (section 4.5) gpuLZ runs before cuSZ's Huffman
  * encoding.  The paper does not print that stage, so its definition here is
  * this library's: a byte-alphabet prefix code, optimal among codes whose
  * lengths do not exceed 12 bits (package-merge; ties: a leaf before a

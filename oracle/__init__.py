@@ -18,7 +18,7 @@ computes, and which passage of the paper it follows, is documented in
   with either matcher;
 * :func:`compress` / :func:`decompress` -- the whole chunked stream;
 * :func:`huff_compress` / :func:`huff_decompress` -- the Huffman stage that
-  follows LZSS in section 4.4's use case (``huffref.h``).
+  follows LZSS in section 4.5's use case (``huffref.h``).
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (brute force, closed forms, hand-worked fixtures, round trip).
@@ -292,7 +292,7 @@ def select_params(sample, dtype_bytes: int, level: int = 3,
     return single if ratio_below(b.size, size) else multi
 
 
-# --- Huffman stage after LZSS (section 4.4's use case), huffref.c ----------------
+# --- Huffman stage after LZSS (section 4.5's use case), huffref.c ----------------
 
 HUFF_MAX_LEN, HUFF_BLOCK, HUFF_SUB = 12, 32768, 1024
 

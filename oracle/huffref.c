@@ -1,6 +1,6 @@
 /*
  * huffref.c -- CPU oracle for the Huffman stage after LZSS (the paper's
- * cuSZ use case, section 4.4).  TEST INFRASTRUCTURE ONLY (see huffref.h).
+ * cuSZ use case, section 4.5).  TEST INFRASTRUCTURE ONLY (see huffref.h).
  *
  * Written for a reader to check by eye: a histogram, package-merge for the
  * length-limited code, canonical code assignment, then bit-by-bit writing

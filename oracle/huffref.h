@@ -1,6 +1,6 @@
 /*
  * huffref.h -- CPU oracle for the Huffman stage that follows LZSS in the
- * paper's use case (section 4.4: cuSZ's Huffman encoding after gpuLZ).
+ * paper's use case (section 4.5: cuSZ's Huffman encoding after gpuLZ).
  *
  * TEST INFRASTRUCTURE ONLY, like lzref.h: only the test suite, the smoke
  * check and the CPU-baseline leg of the benchmark may call it, and it shares

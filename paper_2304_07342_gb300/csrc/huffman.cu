@@ -1,5 +1,5 @@
 // huffman.cu -- the Huffman stage that follows LZSS in the paper's use case
-// (section 4.4: cuSZ Huffman-codes what gpuLZ produces).  Byte alphabet,
+// (section 4.5: cuSZ Huffman-codes what gpuLZ produces).  Byte alphabet,
 // an optimal prefix code limited to kHufMaxLen bits, canonical codes, and
 // the "GHF1" stream described in include/lz.h.
 //
