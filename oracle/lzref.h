@@ -9,8 +9,8 @@
  * What it computes (paper section 2.2, "LZSS", basic steps 1-6, restricted
  * to independent chunks as in section 3.3.1 and to S-byte symbols as in
  * section 3.2.3):
- *   per chunk, from coding position p = 0, find the longest match in the
- *   sliding window of the W previous symbols of the same chunk (nearest
+ *   per chunk, from coding position p = 0, take the longest run that the
+ *   W previous symbols of the same chunk (the window) repeat from p (nearest
  *   offset on ties, match length <= offset, <= max_match, <= symbols left);
  *   emit a pointer (len, off) when len >= min_match, else a literal symbol;
  *   one flag bit per token (1 = pointer, 0 = literal).
