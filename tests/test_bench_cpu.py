@@ -1,0 +1,33 @@
+"""The benchmark's reference arm on the host: the JSON line keeps the
+contract (impl, metric, unit, steps, warm-up, cpu_baseline, e2e with zero
+copies) and its value is the oracle's own throughput over the timed steps."""
+from __future__ import annotations
+
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_line():
+    out = subprocess.run(
+        [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+         "--steps", "2", "--warmup", "1", "--workload", "quant-small"],
+        capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["n_gpus"] == 1
+    assert line["unit"] == "GB/s" and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["ms_per_step"] > 0
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    assert "uint16 quant codes" in cb["sample"] and "2 timed steps" in cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    # a step compresses whole chunks (or the whole input when it is shorter)
+    n = int(cb["sample"].split("first ")[1].split(" bytes")[0])
+    assert n > 0 and (n % 4096 == 0 or n == 1 << 20)
