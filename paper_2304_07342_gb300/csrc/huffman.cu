@@ -575,7 +575,9 @@ __global__ void __launch_bounds__(256) huff_decode_kernel(const uint8_t *in, uin
           v |= next_symbol() << 24;
           w[q] = v;
         }
-        *reinterpret_cast<uint4 *>(out + i) = make_uint4(w[0], w[1], w[2], w[3]);
+        // streaming store: the output should not push the stream's lines,
+        // which the other lanes of the warp still read, out of L2
+        __stcs(reinterpret_cast<uint4 *>(out + i), make_uint4(w[0], w[1], w[2], w[3]));
       }
     }
     for (; i < hi; ++i) out[i] = static_cast<uint8_t>(next_symbol());
