@@ -318,14 +318,19 @@ class Codec:
         s = stream if stream is not None else self.torch.cuda.current_stream(self.device)
         return s.cuda_stream
 
-    @staticmethod
-    def _bytes_of(x):
-        return x.contiguous().view(-1).view(__import__("torch").uint8)
+    def _bytes_of(self, x, stream):
+        """x as a flat contiguous uint8 tensor.  A contiguous copy made here
+        is marked as used by `stream`, so that its memory is not handed out
+        again before the work queued there has read it."""
+        xb = x.contiguous().view(-1).view(self.torch.uint8)
+        if stream is not None and x.numel() and xb.data_ptr() != x.data_ptr():
+            xb.record_stream(stream)
+        return xb
 
     def compress(self, x, p: Params, out=None, out_bytes=None, stream=None,
                  match: int = LZ_MATCH_EXACT, version: int = 1):
         torch = self.torch
-        xb = self._bytes_of(x)
+        xb = self._bytes_of(x, stream)
         cap = lz_compressed_bound(xb.numel(), p)
         if cap == 0:
             raise LzError(LZ_ERR_INVALID_ARG, "lz_compressed_bound")
@@ -341,7 +346,7 @@ class Codec:
     def decompress(self, stream_bytes, n_bytes: int | None = None, out=None,
                    out_bytes=None, in_bytes: int | None = None, stream=None):
         torch = self.torch
-        sb = stream_bytes
+        sb = self._bytes_of(stream_bytes, stream)
         nin = sb.numel() if in_bytes is None else in_bytes
         if out is None:
             if n_bytes is None:
