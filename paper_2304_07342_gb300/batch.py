@@ -65,12 +65,20 @@ def autotuned_params(codec, pools, sample_bytes: int = 8 << 20) -> list:
         s = codec.compress_sync(pool[:n], p)
         out.append(p)
         ratios.append(n / max(1, s.numel()))
-    caps = [p.C for p, r in zip(out, ratios) if r >= 1.05]
-    if caps:
-        cap = max(caps)
-        out = [p if r >= 1.05 or p.C <= cap else lz.Params(p.S, cap, p.W, p.m, p.M)
-               for p, r in zip(out, ratios)]
-    return out
+    return hold_chunks(out, ratios)
+
+
+def hold_chunks(params: list, ratios: list, min_ratio: float = 1.05) -> list:
+    """Per-kind parameters with the chunk of every kind whose sample ratio is
+    below `min_ratio` held to the largest chunk of the kinds at or above it
+    (unchanged when no kind compresses, or when its chunk is already no
+    larger)."""
+    caps = [p.C for p, r in zip(params, ratios) if r >= min_ratio]
+    if not caps:
+        return list(params)
+    cap = max(caps)
+    return [p if r >= min_ratio or p.C <= cap else lz.Params(p.S, cap, p.W, p.m, p.M)
+            for p, r in zip(params, ratios)]
 
 
 def build(torch, n_buffers: int = 10_000, seed: int = 0, params=None, pools=None,
