@@ -125,7 +125,8 @@ uint64_t lz_compressed_bound(uint64_t n_bytes, const lz_params *p);
  * hold header + table + index; if the records do not fit, the stream is
  * incomplete, *d_out_bytes still receives the size that was needed and
  * lz_sync reports LZ_ERR_BUFFER_TOO_SMALL.  Capacity
- * lz_compressed_bound(n_bytes, p) always suffices. */
+ * lz_compressed_bound(n_bytes, p) always suffices.  LZ_ERR_INVALID_ARG
+ * beyond 2^32 - 2^20 - 1 chunks (the work counter is 32 bits wide). */
 lz_status lz_compress(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
                       const lz_params *p, void *d_out, uint64_t out_cap,
                       uint64_t *d_out_bytes, lz_stream_t stream);
@@ -230,7 +231,9 @@ typedef struct lz_batch lz_batch;
  * allocated stream-ordered on `stream` (cudaMallocAsync) and its descriptors
  * uploaded on it, so no device-wide synchronisation happens; runs must be
  * ordered after this call (same stream, or an event).  Errors are those of
- * the single-buffer calls (checked per item) plus LZ_ERR_NOMEM.  The buffers
+ * the single-buffer calls (checked per item) plus LZ_ERR_NOMEM, and
+ * LZ_ERR_INVALID_ARG when a compression batch's items hold more than
+ * 2^32 - 2^20 - 1 chunks together (one 32-bit work counter).  The buffers
  * named by the items must stay valid while the batch is run. */
 lz_status lz_batch_create(lz_ctx *ctx, const lz_batch_item *items, uint32_t n_items,
                           int decompress, lz_stream_t stream, lz_batch **out);

@@ -88,6 +88,10 @@ constexpr int kCompressWarps = 4;      // warps per block (fewer if smem-bound)
 constexpr uint32_t kParkSlots = 3;     // parked records per compressing warp
 constexpr int kDecompressBlock = 256;  // 8 warps, one chunk per warp
 constexpr size_t kScratchHead = 16;
+// Chunks per compression launch: the warps take chunks from a 32-bit work
+// counter and each takes one ticket past the last chunk, so the counter must
+// not wrap; the margin covers 2^20 warps.
+constexpr uint64_t kMaxLaunchChunks = 0xFFFFFFFFull - (1ull << 20);
 
 uint64_t div_up(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 uint32_t round16(uint64_t v) { return static_cast<uint32_t>((v + 15) & ~15ull); }
@@ -269,7 +273,7 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
   const uint32_t S = p->symbol_bytes, C = p->chunk_bytes;
   if (version == 1 && n_bytes % S != 0) return LZ_ERR_INVALID_ARG;  // tails: version 2
   const uint64_t nc = div_up(n_bytes, C);
-  if (nc > 0xFFFFFFFFull) return LZ_ERR_INVALID_ARG;
+  if (nc > kMaxLaunchChunks) return LZ_ERR_INVALID_ARG;
   const uint64_t records_at = glz::kHeaderBytes + glz::kTableEntry * nc +
                               8ull * div_up(nc, glz::kIndexStride);
   if (out_cap < records_at) return LZ_ERR_BUFFER_TOO_SMALL;
@@ -734,6 +738,7 @@ lz_status batch_create_compress(lz_ctx *ctx, const lz_batch_item *items, uint32_
     descs.push_back(d);
     bases.push_back(total);
     total += nc;
+    if (total > kMaxLaunchChunks) return LZ_ERR_INVALID_ARG;
     ps.push_back(*p);
     kmax = std::max<uint64_t>(kmax, p->chunk_bytes / p->symbol_bytes);
     uint32_t j = 1;
