@@ -186,7 +186,10 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    build.build()
+    if rank == 0:
+        build.build()  # a no-op when the library is up to date
+    if world > 1:
+        dist.barrier()  # the other ranks load what rank 0 built
     codec = lz.Codec(local)
     stream = torch.cuda.current_stream()
 
