@@ -612,9 +612,13 @@ def _e2e(codec, items, stream, args):
         for ev in done:
             stream.wait_event(ev)
 
+    rank, world, local = _dist()
     try:
         one()
         torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -632,12 +636,22 @@ def _e2e(codec, items, stream, args):
         for cd in codecs[1:]:
             cd.close()
     ms = a.elapsed_time(b) / steps
+    if world > 1:  # every rank's bytes over the slowest rank's time
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
     n_in = sum(it["d_in"].numel() for it in items)
     n_out = sum(it["size"] for it in items)
+    link = _link_bandwidth(items, pinned_in, pinned_out, streams)
+    if world > 1:  # the whole job's bytes
+        t = torch.tensor([n_in, n_out], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        n_in, n_out = (int(v) for v in t.tolist())
     return {"value": round(n_in / (ms * 1e-3) / 1e9, 3), "unit": "GB/s",
             "h2d_bytes_per_step": int(n_in),
             "d2h_bytes_per_step": int(n_out),
-            "link": _link_bandwidth(items, pinned_in, pinned_out, streams),
+            "link": link,
             "note": "one stream and context per item; the stream size is known from the "
                     "warm-up pass and D2H copies exactly that many bytes"}
 
