@@ -198,8 +198,14 @@ lz_status lz_decompress(lz_ctx *ctx, const void *d_in, uint64_t in_bytes,
  * (other streams, other threads) race and must not be issued; calls ordered
  * on one stream are fine.  The first call on a device looks up the array's
  * device address (and launch limits); make that first call before any
- * stream capture.  Slower than lz_compress on inputs with uneven chunks: a
- * chunk whose offset is not yet known waits instead of moving on. */
+ * stream capture.  Under CUDA's lazy module loading (the default) the first
+ * launch of each kernel variant loads its code onto the device, which takes
+ * device memory: before entering a region where nothing may be allocated,
+ * make one call for every symbol size and window class it will use (window
+ * classes: W <= 32, <= 64, <= 128, <= 256, <= 512, <= 1024), plus one with
+ * n_bytes = 0 if empty inputs occur.  Slower than lz_compress on inputs with
+ * uneven chunks: a chunk whose offset is not yet known waits instead of
+ * moving on. */
 lz_status lz_compress_noalloc(const void *d_in, uint64_t n_bytes, const lz_params *p,
                               void *d_out, uint64_t out_cap, uint64_t *d_out_bytes,
                               lz_stream_t stream);

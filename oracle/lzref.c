@@ -93,50 +93,45 @@ void lzref_longest_match(const uint8_t *chunk, uint32_t k, uint32_t p,
 }
 
 /* The paper's own matcher (section 3.3.2, the four steps of its matching
- * method), over S-byte symbols.  Two pointers: the search pointer starts
- * at the beginning of the window, the position pointer at the coding
- * position p.
- *   - While the two point at equal symbols, both advance (a run); the
- *     offset of the run is the distance between them when it started.
- *   - At a mismatch the run ends: it is recorded if strictly longer than
- *     the longest so far; the position pointer goes back to p and the
- *     search pointer advances by one from where it stopped (it is never
- *     moved back, which is why the method can miss the longest match).
- *   - Before a run starts, a mismatch just advances the search pointer.
- *   - The scan ends when the search pointer reaches p (so a match never
- *     runs into the coding position: length <= offset) or the position
- *     pointer reaches the end of the look-ahead.
- * Readings where the printed loop is silent: the look-ahead ends at the
- * chunk end or M symbols after p, whichever comes first (the length field
- * is one byte); a run still in progress when the scan ends is compared
- * like any other (otherwise a run that reaches p would never count).
- * Ties keep the first run found, i.e. the farthest offset. */
+ * method), over S-byte symbols, stated run by run.  The scan goes through
+ * the window from its far end, p - min(W, p), towards the coding position
+ * p:
+ *   1. the next window symbol equal to the one at p starts a run (no other
+ *      symbol can start one);
+ *   2. the run is measured: the number of symbols that agree with the
+ *      look-ahead from p, stopping at a mismatch, when the run would reach
+ *      p (so length <= offset) or at the end of the look-ahead;
+ *   3. a run strictly longer than the longest so far replaces it, with
+ *      offset p - (run start);
+ *   4. a run that reached p or the look-ahead end ends the scan; otherwise
+ *      the scan resumes just after the symbol that broke the run -- that
+ *      symbol itself is never tried as a run start, and the scan never
+ *      goes back into the run, which is why the method can miss the
+ *      longest match.
+ * Readings where the paper is silent: the look-ahead ends at the chunk end
+ * or M symbols after p, whichever comes first (the length field is one
+ * byte); the run that ends the scan is compared like any other (otherwise
+ * a run that reaches p would never count).  Ties keep the first run found,
+ * i.e. the farthest offset. */
 void lzref_paper_match(const uint8_t *chunk, uint32_t k, uint32_t p,
                        uint32_t S, uint32_t W, uint32_t M, uint32_t *len,
                        uint32_t *off) {
-  uint32_t search = p > W ? p - W : 0;
-  uint32_t ahead_end = (k - p < M) ? k : p + M;
-  uint32_t pos = p;
-  uint32_t run = 0, run_off = 0, best = 0, best_off = 0;
-  while (search < p && pos < ahead_end) {
-    if (ref_sym_eq(chunk, S, pos, search)) {
-      if (run == 0) run_off = pos - search;
-      ++run;
-      ++pos;
-    } else {
-      if (run > best) {
-        best = run;
-        best_off = run_off;
-      }
-      run = 0;
-      run_off = 0;
-      pos = p;
+  const uint32_t end = (k - p < M) ? k : p + M;  /* look-ahead end */
+  uint32_t best = 0, best_off = 0;
+  uint32_t w = p > W ? p - W : 0;
+  while (w < p) {
+    if (!ref_sym_eq(chunk, S, w, p)) { /* step 1: not a run start */
+      ++w;
+      continue;
     }
-    ++search;
-  }
-  if (run > best) {
-    best = run;
-    best_off = run_off;
+    uint32_t l = 0; /* step 2 */
+    while (w + l < p && p + l < end && ref_sym_eq(chunk, S, w + l, p + l)) ++l;
+    if (l > best) { /* step 3 */
+      best = l;
+      best_off = p - w;
+    }
+    if (w + l == p || p + l == end) break; /* step 4 */
+    w += l + 1;
   }
   *len = best;
   *off = best_off;

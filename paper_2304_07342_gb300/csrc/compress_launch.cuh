@@ -4,46 +4,10 @@
 
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "compress_impl.cuh"
+#include "launch_cache.cuh"
 
 namespace glz {
-
-// Launch-shape cache for one kernel instance (the smem opt-in and the
-// occupancy query are done once per block/smem combination).
-struct LaunchCache {
-  std::mutex mu;
-  int block = -1, per_sm = 0, sms = 0;
-  size_t smem = 0;
-};
-
-// Blocks of `kern` resident per SM for this block and smem size.
-template <typename K>
-static cudaError_t resident_blocks(LaunchCache &lc, K kern, int block,
-                                   size_t smem, int *per_sm, int *sms) {
-  std::lock_guard<std::mutex> lock(lc.mu);
-  if (lc.block == block && lc.smem == smem) {
-    *per_sm = lc.per_sm;
-    *sms = lc.sms;
-    return cudaSuccess;
-  }
-  cudaError_t e = cudaFuncSetAttribute(
-      kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, block, smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0;
-  e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  lc.block = block;
-  lc.smem = smem;
-  lc.per_sm = *per_sm;
-  lc.sms = *sms;
-  return cudaSuccess;
-}
 
 template <int S, int NJ>
 static cudaError_t launch_compress_nj(const CompressArgs &A, int block, unsigned grid_req,

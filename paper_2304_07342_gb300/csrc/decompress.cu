@@ -7,26 +7,32 @@
 //   * the record offset is the superblock index entry plus the record sizes
 //     of the (at most 63) chunks before it in its superblock -- no scan
 //     across the whole stream;
-//   * tokens are decoded 32 at a time (lane = token): the flag bits give
-//     each token's payload offset by popcount, a shuffle scan of token
-//     lengths gives each token's output position;
-//   * output positions are then produced 32 at a time (lane = position):
-//     the owning token is found by a binary search over the 32 token start
-//     positions (shuffles); a position inside a pointer copies from
-//     position - offset, and chains whose source lies in the same 32
-//     positions are resolved by pointer jumping (five shuffle rounds);
-//     older sources are read from a ring of the last >= W+32 decoded
-//     symbols in shared memory (offsets are at most W);
-//   * the record (flags + payload) is first staged into the warp's shared
-//     slice with a TMA bulk copy, so token decoding reads shared memory;
-//   * symbols are stored straight to the output, 32*S contiguous bytes per
-//     warp instruction.
+//   * the record (flags + payload) is staged into the warp's shared slice
+//     with a TMA bulk copy; a chunk without pointers (or a stored chunk of
+//     stream version 2) is copied straight out with 16-byte stores;
+//   * otherwise the chunk is decoded into a shared-memory image of its
+//     output in two phases.  Phase 1 takes the tokens 32 at a time (lane =
+//     token): the flag word gives each token's payload offset by popcount,
+//     a shuffle scan of token lengths gives its output position; a literal
+//     writes its symbol there, a pointer writes (offset - 1) into the slot
+//     of its first symbol, and both set their bit in a token-start bitmap
+//     (pointers also in a pointer-start bitmap).  Phase 2 takes the output
+//     positions 32 at a time (lane = position): the owning token is the
+//     last set start bit at or before the position (one bit scan; a token
+//     that began in an earlier round is carried in registers), a position
+//     inside a pointer copies from position - offset, and sources inside
+//     the same 32 positions are resolved by pointer jumping over the lanes;
+//     earlier positions are final, later rounds read them;
+//   * the image is copied out with 16-byte stores.
+// Pointers never reach before their own chunk, so chunks are independent
+// (section 3.3.1).  When the slice cannot hold the output image and the
+// record window (very large chunks), the same two phases run on the output
+// buffer itself and read the record in place.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "glz_common.h"
 #include "glz_device.cuh"
+#include "launch_cache.cuh"
 
 namespace glz {
 
@@ -61,17 +67,6 @@ __device__ __forceinline__ bool read_header(const uint8_t *in, Header &h) {
   return ok;
 }
 
-__device__ __forceinline__ void store_symbol(uint8_t *dst, uint32_t v,
-                                             uint32_t S, bool aligned) {
-  if (aligned && S == 4) {
-    *reinterpret_cast<uint32_t *>(dst) = v;
-  } else if (aligned && S == 2) {
-    *reinterpret_cast<uint16_t *>(dst) = static_cast<uint16_t>(v);
-  } else {
-    for (uint32_t i = 0; i < S; ++i) dst[i] = static_cast<uint8_t>(v >> (8 * i));
-  }
-}
-
 // Sum of the record sizes of chunks [lo, hi) (hi - lo <= 64).
 __device__ __forceinline__ uint64_t record_bytes(const uint8_t *table,
                                                  uint32_t lo, uint32_t hi,
@@ -85,10 +80,47 @@ __device__ __forceinline__ uint64_t record_bytes(const uint8_t *table,
   return warp_sum_u64(part);
 }
 
-// Worst-case record of a chunk of k symbols (flags + payload).
+// Worst-case record of a chunk of k symbols (flags + payload, no tail).
 __device__ __forceinline__ uint64_t record_bound(uint64_t k, const Header &h) {
   const uint64_t extra = (1u + h.offB > h.S * h.m) ? (1u + h.offB - h.S * h.m) : 0u;
   return (k + 7) / 8 + static_cast<uint64_t>(h.S) * k + extra * (k / h.m);
+}
+
+// Little-endian 32-bit word at any byte address of shared memory (the two
+// aligned words around it; may read up to 3 bytes past the addressed ones).
+__device__ __forceinline__ uint32_t ld_u32_any(const uint8_t *p) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uint32_t *w = reinterpret_cast<const uint32_t *>(a & ~static_cast<uintptr_t>(3));
+  const uint32_t sh = 8u * static_cast<uint32_t>(a & 3u);
+  return sh ? __funnelshift_r(w[0], w[1], sh) : w[0];
+}
+
+// Symbol slot j of an output image (S-byte aligned) or of an output buffer
+// of any alignment.
+template <int S>
+__device__ __forceinline__ uint32_t ld_slot(const uint8_t *o, uint32_t j, bool aligned) {
+  const uint8_t *p = o + static_cast<uint64_t>(j) * S;
+  if constexpr (S == 1) return *p;
+  if (aligned) {
+    if constexpr (S == 2) return *reinterpret_cast<const uint16_t *>(p);
+    else return *reinterpret_cast<const uint32_t *>(p);
+  }
+  return static_cast<uint32_t>(ld_le(p, S));
+}
+
+template <int S>
+__device__ __forceinline__ void st_slot(uint8_t *o, uint32_t j, uint32_t v, bool aligned) {
+  uint8_t *p = o + static_cast<uint64_t>(j) * S;
+  if constexpr (S == 1) {
+    *p = static_cast<uint8_t>(v);
+    return;
+  }
+  if (aligned) {
+    if constexpr (S == 2) *reinterpret_cast<uint16_t *>(p) = static_cast<uint16_t>(v);
+    else *reinterpret_cast<uint32_t *>(p) = v;
+    return;
+  }
+  for (uint32_t i = 0; i < S; ++i) p[i] = static_cast<uint8_t>(v >> (8 * i));
 }
 
 // Copy record bytes [src, src + n) into the warp's window so that the copy
@@ -151,12 +183,162 @@ __device__ __forceinline__ void copy_s2g(uint8_t *dst, const uint8_t *src,
   for (uint32_t i = done + lane; i < n; i += 32) dst[i] = src[i];
 }
 
-__device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
-                                             const Header &h, uint32_t c,
-                                             uint64_t records_at,
-                                             uint32_t *ring, uint32_t rmask,
-                                             uint8_t *win, uint64_t *bar,
-                                             uint32_t &phase, uint32_t lane) {
+
+// A warp's shared-memory slice (see DecodeLayout).
+struct Slice {
+  uint64_t *bar;
+  uint32_t *sbits, *mbits;  // token starts, pointer starts (one bit per position)
+  uint8_t *hi;              // high bytes of (offset - 1), or nullptr
+  uint8_t *outb;            // output image, or nullptr (decode into the output)
+  uint8_t *win;             // record window, or nullptr (read the record in place)
+  uint32_t phase;           // parity of the next TMA completion on bar
+};
+
+__device__ __forceinline__ Slice make_slice(uint8_t *ws, const DecodeLayout &L, bool hi) {
+  Slice sl;
+  sl.bar = reinterpret_cast<uint64_t *>(ws);
+  sl.sbits = reinterpret_cast<uint32_t *>(ws + L.bits_off);
+  sl.mbits = sl.sbits + L.bit_words;
+  sl.hi = hi ? ws + L.hi_off : nullptr;
+  sl.outb = L.staged ? ws + L.out_off : nullptr;
+  sl.win = L.staged ? ws + L.win_off : nullptr;
+  sl.phase = 0;
+  return sl;
+}
+
+// Phases 1 and 2 for a chunk of k symbols with ntok tokens whose payload
+// holds pay_tok bytes of tokens: the symbols are written into `ob` (the
+// output image, or the output itself).  STAGED: the record is in shared
+// memory (words may be read up to 3 bytes past it).  False when the tokens
+// are inconsistent (corrupt stream); nothing outside the chunk's output and
+// the slice is written either way.
+template <int S, bool STAGED>
+__device__ __forceinline__ bool decode_tokens(const Header &h, const uint8_t *flags,
+                                              const uint8_t *payload, uint32_t ntok,
+                                              uint32_t pay_tok, uint32_t k, uint8_t *ob,
+                                              bool aligned, const Slice &sl, uint32_t lane) {
+  const uint32_t tsz = 1u + h.offB;
+  const uint32_t offmask = h.offB == 2 ? 0xFFFFu : 0xFFu;
+  const uint32_t lt = lanemask_lt(lane);
+  const uint32_t fb = (ntok + 7) / 8;
+  const uint32_t nw = (k + 31) / 32;
+  uint32_t *sbits = sl.sbits, *mbits = sl.mbits;
+  for (uint32_t i = lane; i < nw; i += 32) {
+    sbits[i] = 0;
+    mbits[i] = 0;
+  }
+  __syncwarp();
+
+  // Phase 1: tokens, 32 at a time (lane = token)
+  uint32_t pos = 0, payu = 0;
+  for (uint32_t tb = 0; tb < ntok; tb += 32) {
+    const uint32_t nv = min(32u, ntok - tb);
+    const uint32_t vm = nv == 32 ? kFull : ((1u << nv) - 1u);
+    uint32_t fw;
+    if constexpr (STAGED) {
+      fw = ld_u32_any(flags + (tb >> 3));
+    } else {
+      fw = 0;
+      for (uint32_t i = 0; i < 4; ++i)
+        if ((tb >> 3) + i < fb) fw |= static_cast<uint32_t>(flags[(tb >> 3) + i]) << (8 * i);
+    }
+    fw &= vm;
+    const uint32_t nm = __popc(fw);
+    const uint32_t gpay = S * (nv - nm) + tsz * nm;
+    if (payu + gpay > pay_tok) return false;
+    const bool valid = lane < nv;
+    const bool ism = (fw >> lane) & 1u;
+    const uint32_t nmb = __popc(fw & lt);
+    const uint32_t my_off = payu + S * (lane - nmb) + tsz * nmb;
+    uint32_t w = 0;
+    if (valid) {
+      if constexpr (STAGED) w = ld_u32_any(payload + my_off);
+      else w = static_cast<uint32_t>(ld_le(payload + my_off, ism ? tsz : S));
+    }
+    const uint32_t len = ism ? (w & 0xFFu) : (valid ? 1u : 0u);
+    const uint32_t off = ism ? ((w >> 8) & offmask) + 1u : 0u;
+    uint32_t x = len;  // inclusive scan of token lengths
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, x, o);
+      if (lane >= static_cast<uint32_t>(o)) x += y;
+    }
+    const uint32_t glen = __shfl_sync(kFull, x, 31);
+    const uint32_t start = pos + x - len;
+    const bool tbad = ism && (len == 0 || off > h.W || (len > off && !h.overlap) || off > start);
+    if (__any_sync(kFull, tbad) || pos + glen > k) return false;
+    if (valid) {
+      const uint32_t bit = 1u << (start & 31u);
+      atomicOr(&sbits[start >> 5], bit);
+      if (ism) {
+        atomicOr(&mbits[start >> 5], bit);
+        st_slot<S>(ob, start, off - 1u, aligned);
+        if (S == 1 && sl.hi) sl.hi[start] = static_cast<uint8_t>((off - 1u) >> 8);
+      } else {
+        st_slot<S>(ob, start, w, aligned);
+      }
+    }
+    pos += glen;
+    payu += gpay;
+  }
+  if (pos != k || payu != pay_tok) return false;
+  __syncwarp();
+
+  // Phase 2: positions, 32 at a time (lane = position)
+  const uint32_t le = lt | (1u << lane);
+  bool cm = false;    // the token owning the previous round's last position is a pointer
+  uint32_t coff = 0;  // and its offset
+  for (uint32_t r0 = 0; r0 < k; r0 += 32) {
+    const uint32_t j = r0 + lane;
+    const bool act = j < k;
+    const uint32_t sw = sbits[r0 >> 5], mw = mbits[r0 >> 5];
+    uint32_t raw = act ? ld_slot<S>(ob, j, aligned) : 0u;
+    if (S == 1 && sl.hi && act) raw |= static_cast<uint32_t>(sl.hi[j]) << 8;
+    const uint32_t mb = sw & le;
+    const uint32_t ol = (31u - __clz(mb)) & 31u;  // owner's lane when mb != 0
+    const uint32_t oraw = __shfl_sync(kFull, raw, ol);
+    const bool om = mb ? ((mw >> ol) & 1u) != 0 : cm;
+    const uint32_t off = mb ? oraw + 1u : coff;
+    cm = __shfl_sync(kFull, om ? 1u : 0u, 31) != 0;
+    coff = __shfl_sync(kFull, off, 31);
+    const bool ptr = act && om;
+    uint32_t f = ptr ? j - off : j;
+    if (__any_sync(kFull, ptr && f >= r0)) {
+      // sources inside this round: jump until every source is a literal of
+      // the round or lies before it (chains shrink, so at most 5 rounds)
+      while (true) {
+        const uint32_t g = __shfl_sync(kFull, f, f >= r0 ? f - r0 : lane);
+        const bool moved = g != f;
+        f = g;
+        if (!__any_sync(kFull, moved)) break;
+      }
+    }
+    if (ptr) st_slot<S>(ob, j, ld_slot<S>(ob, f, aligned), aligned);
+    __syncwarp();
+  }
+  return true;
+}
+
+template <bool STAGED>
+__device__ __forceinline__ bool decode_tokens_s(const Header &h, const uint8_t *flags,
+                                                const uint8_t *payload, uint32_t ntok,
+                                                uint32_t pay_tok, uint32_t k, uint8_t *ob,
+                                                bool aligned, const Slice &sl, uint32_t lane) {
+  switch (h.S) {
+    case 1:
+      return decode_tokens<1, STAGED>(h, flags, payload, ntok, pay_tok, k, ob, aligned, sl, lane);
+    case 2:
+      return decode_tokens<2, STAGED>(h, flags, payload, ntok, pay_tok, k, ob, aligned, sl, lane);
+    default:
+      return decode_tokens<4, STAGED>(h, flags, payload, ntok, pay_tok, k, ob, aligned, sl, lane);
+  }
+}
+
+// One chunk.  Returns false when a TMA copy did not complete in time (the
+// warp must stop: its barrier phase is unknown).
+__device__ __forceinline__ bool decode_chunk(const DecompressArgs &A, const Header &h,
+                                             uint32_t c, uint64_t records_at, Slice &sl,
+                                             uint32_t lane) {
   const uint8_t *in = A.in;
   const uint8_t *table = in + kHeaderBytes;
   const uint8_t *index = table + 8ull * h.nc;
@@ -189,10 +371,10 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
     return true;
   }
   const uint8_t *flags = in + rec_at;  // read in place when there is no window
-  if (win) {
+  if (sl.win) {
     bool staged;
-    flags = stage_record(in + rec_at, static_cast<uint32_t>(fb + pay), win, bar, phase,
-                         lane, staged);
+    flags = stage_record(in + rec_at, static_cast<uint32_t>(fb + pay), sl.win, sl.bar,
+                         sl.phase, lane, staged);
     if (!staged) {
       if (lane == 0) atomicOr(A.err, kErrTimeout);
       return false;
@@ -201,126 +383,60 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A,
   const uint8_t *payload = flags + fb;
   uint8_t *dst = A.out + chunk_at;
   if (stored) {
-    if (win) {
+    if (sl.win) {
       copy_s2g(dst, payload, pay, lane);  // the window has slack past the record
     } else {
       for (uint32_t i = lane; i < pay; i += 32) dst[i] = payload[i];
     }
     return true;
   }
-  const uint32_t S = h.S, offB = h.offB, tsz = 1 + h.offB;
-  if (win) {
-    // a chunk without pointers is its payload: copy it straight out
-    uint32_t any = 0;
-    for (uint32_t i = lane; i < fb; i += 32) any |= flags[i];
-    if (!__any_sync(kFull, any != 0)) {
-      if (ntok != k || pay != bytes_c) {
-        if (lane == 0) atomicOr(A.err, kErrCorrupt);
-        return true;
-      }
-      copy_s2g(dst, flags + fb, pay, lane);
-      return true;
-    }
-  }
-  const bool aligned = A.out_aligned != 0;
-  const uint32_t lt = lanemask_lt(lane);
-
-  uint32_t pos = 0;       // symbols produced
-  uint64_t pay_used = 0;  // payload bytes consumed
-  const uint32_t pay_tok = pay - tail;  // the tokens' payload; the tail follows it
-  for (uint32_t tb = 0; tb < ntok; tb += 32) {
-    const uint32_t t = tb + lane;
-    const bool valid = t < ntok;
-    const bool ism = valid && ((flags[t >> 3] >> (t & 7)) & 1u);
-    const uint32_t mm = __ballot_sync(kFull, ism);
-    const uint32_t vm = __ballot_sync(kFull, valid);
-    const uint32_t nmb = __popc(mm & lt);
-    const uint32_t nlb = __popc(vm & ~mm & lt);
-    const uint64_t my_off = pay_used + S * nlb + tsz * nmb;
-    const uint32_t my_sz = ism ? tsz : (valid ? S : 0u);
-    bool tbad = valid && my_off + my_sz > pay_tok;
-    uint32_t len = valid ? 1u : 0u, off = 0, val = 0;
-    if (valid && !tbad) {
-      if (ism) {
-        len = payload[my_off];
-        off = payload[my_off + 1];
-        if (offB == 2) off |= static_cast<uint32_t>(payload[my_off + 2]) << 8;
-        off += 1;
-      } else {
-        val = static_cast<uint32_t>(ld_le(payload + my_off, S));
-      }
-    }
-    tbad = tbad || (ism && (len == 0 || off > h.W || (len > off && !h.overlap)));
-    // inclusive scan of token lengths -> output start of each token
-    uint32_t x = len;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, x, o);
-      if (lane >= static_cast<uint32_t>(o)) x += y;
-    }
-    const uint32_t group_len = __shfl_sync(kFull, x, 31);
-    const uint32_t start = pos + x - len;
-    tbad = tbad || (ism && off > start);
-    tbad = tbad || pos + group_len > k;
-    if (__any_sync(kFull, tbad)) {
+  // a chunk without pointers is its payload: copy it straight out
+  uint32_t any = 0;
+  for (uint32_t i = lane; i < fb; i += 32) any |= flags[i];
+  if (!__any_sync(kFull, any != 0)) {
+    if (ntok != k || pay != bytes_c) {
       if (lane == 0) atomicOr(A.err, kErrCorrupt);
       return true;
     }
-    const uint32_t end = pos + group_len;
-    if (mm == 0) {
-      // all literals: lane i produces symbol pos + i
-      if (valid) {
-        ring[(pos + lane) & rmask] = val;
-        store_symbol(dst + static_cast<uint64_t>(pos + lane) * S, val, S, aligned);
-      }
+    if (sl.win) {
+      copy_s2g(dst, payload, pay, lane);
     } else {
-      const uint32_t start_key = valid ? start : kFull;
-      for (uint32_t r0 = pos; r0 < end; r0 += 32) {
-        const uint32_t jp = r0 + lane;
-        const bool active = jp < end;
-        // owning token: the last lane whose start is <= jp
-        uint32_t lo = 0;
-#pragma unroll
-        for (uint32_t step = 16; step > 0; step >>= 1) {
-          const uint32_t s = __shfl_sync(kFull, start_key, lo + step);
-          if (s <= jp) lo += step;
-        }
-        const uint32_t o_ism = __shfl_sync(kFull, ism ? 1u : 0u, lo);
-        const uint32_t o_off = __shfl_sync(kFull, off, lo);
-        const uint32_t o_val = __shfl_sync(kFull, val, lo);
-        uint32_t f = (active && o_ism) ? jp - o_off : jp;
-        // resolve sources inside these 32 positions by pointer jumping
-#pragma unroll
-        for (int it = 0; it < 5; ++it) {
-          const uint32_t src_lane = f >= r0 ? f - r0 : lane;
-          const uint32_t g = __shfl_sync(kFull, f, src_lane);
-          if (f >= r0) f = g;
-        }
-        const uint32_t v_here = __shfl_sync(kFull, o_val, f >= r0 ? f - r0 : lane);
-        const uint32_t v = f >= r0 ? v_here : ring[f & rmask];
-        __syncwarp();
-        if (active) {
-          ring[jp & rmask] = v;
-          store_symbol(dst + static_cast<uint64_t>(jp) * S, v, S, aligned);
-        }
-        __syncwarp();
-      }
+      for (uint32_t i = lane; i < pay; i += 32) dst[i] = payload[i];
     }
-    __syncwarp();
-    pos = end;
-    pay_used += S * __popc(vm & ~mm) + tsz * __popc(mm);
+    return true;
   }
-  if (pos != k || pay_used != pay_tok) {
+  const uint32_t pay_tok = pay - tail;  // the tokens' payload; the tail follows it
+  bool ok;
+  if (sl.win) {
+    ok = decode_tokens_s<true>(h, flags, payload, ntok, pay_tok, k, sl.outb, true, sl, lane);
+  } else {
+    const bool aligned = A.out_aligned != 0 && (h.C % 4) == 0;
+    ok = decode_tokens_s<false>(h, flags, payload, ntok, pay_tok, k, dst, aligned, sl, lane);
+  }
+  if (!ok) {
     if (lane == 0) atomicOr(A.err, kErrCorrupt);
-  } else if (lane < tail) {
-    dst[static_cast<uint64_t>(k) * S + lane] = payload[pay_tok + lane];
+    return true;
   }
+  uint8_t *ob = sl.win ? sl.outb : dst;
+  if (lane < tail) ob[static_cast<uint64_t>(k) * h.S + lane] = payload[pay_tok + lane];
+  if (sl.win) {
+    __syncwarp();
+    copy_s2g(dst, sl.outb, bytes_c, lane);
+  }
+  __syncwarp();
   return true;
+}
+
+// Per-warp slice for a stream with header h.
+__device__ __forceinline__ DecodeLayout layout_of(const Header &h, uint64_t budget) {
+  const uint64_t k = h.C / h.S;
+  return decode_layout(k, h.C, decode_record_bound(k, h.S, h.offB, h.m), h.S == 1 && h.offB == 2,
+                       budget);
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) decompress_kernel(const DecompressArgs A) {
+__global__ void __launch_bounds__(1024, 1) decompress_kernel(const DecompressArgs A) {
   extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = threadIdx.x >> 5;
@@ -344,39 +460,27 @@ __global__ void __launch_bounds__(256) decompress_kernel(const DecompressArgs A)
     return;
   }
   if (leader) *A.out_bytes = h.n;
-  // per-warp slice, decided from the header: mbarrier, a ring of >= W + 32
-  // decoded symbols (offsets are at most W), and a window for one record
-  uint32_t ring_n = 64;
-  while (ring_n < h.W + 32) ring_n <<= 1;
-  const uint32_t rmask = ring_n - 1;
-  const uint64_t kfull = h.C / h.S;
-  uint64_t need = 16 + 4ull * ring_n + ((record_bound(kfull, h) + 32 + 15) & ~15ull);
-  // a record too large for one warp's window is read from global memory
-  const bool windowed = need <= A.smem_bytes;
-  if (!windowed) need = 16 + 4ull * ring_n;
-  const uint64_t fit = A.smem_bytes / need;
-  const uint32_t active = fit < wpb ? static_cast<uint32_t>(fit) : wpb;
+  // per-warp slice, decided from the header; warps that do not fit sit out
+  const DecodeLayout L = layout_of(h, A.smem_bytes);
+  const uint32_t fit = A.smem_bytes / L.per_warp;
+  const uint32_t active = fit < wpb ? fit : wpb;
   if (warp >= active) return;
-  uint8_t *ws = smem + warp * need;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(ws);
-  uint32_t *ring = reinterpret_cast<uint32_t *>(ws + 16);
-  uint8_t *win = windowed ? ws + 16 + 4ull * ring_n : nullptr;
+  Slice sl = make_slice(smem + static_cast<uint64_t>(warp) * L.per_warp, L,
+                        h.S == 1 && h.offB == 2);
   if (lane == 0) {
-    mbar_init(bar, 1);
+    mbar_init(sl.bar, 1);
     fence_mbar_init();
   }
   __syncwarp();
-  uint32_t phase = 0;
-
   const uint32_t gw = blockIdx.x * active + warp;
   const uint32_t nwarps = gridDim.x * active;
   for (uint32_t c = gw; c < h.nc; c += nwarps)
-    if (!decode_chunk(A, h, c, records_at, ring, rmask, win, bar, phase, lane)) break;
+    if (!decode_chunk(A, h, c, records_at, sl, lane)) break;
 }
 
 // Batched decompression: chunks of all streams in order, grid-stride; each
 // warp finds its stream by a 32-way search over the streams' first chunks.
-__global__ void __launch_bounds__(256) decompress_batch_kernel(const DecompressBatchArgs B) {
+__global__ void __launch_bounds__(1024, 1) decompress_batch_kernel(const DecompressBatchArgs B) {
   extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = threadIdx.x >> 5;
@@ -388,20 +492,16 @@ __global__ void __launch_bounds__(256) decompress_batch_kernel(const DecompressB
       *B.empties[i].out_bytes = 0;
     }
   }
-  const uint64_t need = 16 + 4ull * B.ring_n + B.win_bytes;
-  const uint64_t fit = B.smem_bytes / need;
-  const uint32_t active = fit < wpb ? static_cast<uint32_t>(fit) : wpb;
+  const uint32_t fit = B.smem_bytes / B.lay.per_warp;
+  const uint32_t active = fit < wpb ? fit : wpb;
   if (warp >= active) return;
-  uint8_t *ws = smem + warp * need;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(ws);
-  uint32_t *ring = reinterpret_cast<uint32_t *>(ws + 16);
-  uint8_t *win = ws + 16 + 4ull * B.ring_n;
+  // the slice covers every stream; the high-byte area exists when any needs it
+  Slice base = make_slice(smem + static_cast<uint64_t>(warp) * B.lay.per_warp, B.lay, false);
   if (lane == 0) {
-    mbar_init(bar, 1);
+    mbar_init(base.bar, 1);
     fence_mbar_init();
   }
   __syncwarp();
-  uint32_t phase = 0;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * active;
   for (uint64_t g = static_cast<uint64_t>(blockIdx.x) * active + warp; g < B.total_chunks;
        g += stride) {
@@ -421,11 +521,15 @@ __global__ void __launch_bounds__(256) decompress_batch_kernel(const DecompressB
     const bool ok = it.in_bytes >= kHeaderBytes && read_header(it.in, h);
     const uint64_t records_at = kHeaderBytes + 8ull * h.nc +
                                 8ull * ((h.nc + kIndexStride - 1) / kIndexStride);
-    uint32_t ring_need = 64;
-    while (ring_need < h.W + 32) ring_need <<= 1;
     // the header must still be the one the plan sized the slices for
-    const bool fits = ok && h.nc == it.nc && ring_need <= B.ring_n &&
-                      record_bound(h.C / h.S, h) + 32 <= B.win_bytes &&
+    const uint64_t kh = ok ? h.C / h.S : 0;
+    const bool need_hi = ok && h.S == 1 && h.offB == 2;
+    const bool fits = ok && h.nc == it.nc && (kh + 31) / 32 <= B.lay.bit_words &&
+                      (!need_hi || B.lay.out_off - B.lay.hi_off >= kh) &&
+                      (!B.lay.staged ||
+                       (h.C + 16 <= B.lay.win_off - B.lay.out_off &&
+                        decode_record_bound(kh, h.S, h.offB, h.m) + 64 <=
+                            B.lay.per_warp - B.lay.win_off)) &&
                       records_at <= it.in_bytes && h.n <= it.out_cap;
     if (!fits) {
       if (lane == 0) atomicOr(B.err, h.n > it.out_cap && ok ? kErrSmall : kErrCorrupt);
@@ -440,34 +544,22 @@ __global__ void __launch_bounds__(256) decompress_batch_kernel(const DecompressB
     A.out_bytes = it.out_bytes;
     A.err = B.err;
     A.out_aligned = static_cast<int>(it.out_aligned);
-    if (!decode_chunk(A, h, c, records_at, ring, B.ring_n - 1, win, bar, phase, lane)) break;
+    base.hi = need_hi ? smem + static_cast<uint64_t>(warp) * B.lay.per_warp + B.lay.hi_off
+                      : nullptr;
+    if (!decode_chunk(A, h, c, records_at, base, lane)) break;
   }
 }
 
+// Warps per decoding block: one block per SM holds as many warp slices as
+// its shared memory allows.
+constexpr int kDecodeBlock = 1024;
+
 cudaError_t launch_decompress_batch(DecompressBatchArgs B, int block, cudaStream_t stream) {
-  static std::mutex mu;
-  static int per_sm = 0, sms = 0, cached_block = -1;
-  static uint32_t cached_smem = 0;
+  static LaunchCache lc;
   const size_t smem = B.smem_bytes;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    if (cached_block != block || cached_smem != B.smem_bytes) {
-      cudaError_t e = cudaFuncSetAttribute(decompress_batch_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(smem));
-      if (e != cudaSuccess) return e;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decompress_batch_kernel,
-                                                        block, smem);
-      if (e != cudaSuccess) return e;
-      int dev = 0;
-      e = cudaGetDevice(&dev);
-      if (e != cudaSuccess) return e;
-      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e != cudaSuccess) return e;
-      cached_block = block;
-      cached_smem = B.smem_bytes;
-    }
-  }
+  int per_sm = 0, sms = 0;
+  cudaError_t e = resident_blocks(lc, decompress_batch_kernel, block, smem, &per_sm, &sms);
+  if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const uint64_t warps = block / 32;
   uint64_t want = (B.total_chunks + warps - 1) / warps;
@@ -478,32 +570,12 @@ cudaError_t launch_decompress_batch(DecompressBatchArgs B, int block, cudaStream
   return cudaGetLastError();
 }
 
-// Shared memory per block; each warp takes a slice sized from the header.
-constexpr uint32_t kDecodeSmemPerBlock = 72 * 1024;
-
 cudaError_t launch_decompress(DecompressArgs A, int block, cudaStream_t stream) {
-  static std::mutex mu;
-  static int per_sm = 0, sms = 0, cached_block = -1;
-  A.smem_bytes = kDecodeSmemPerBlock;
-  const size_t smem = kDecodeSmemPerBlock;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    if (cached_block != block) {
-      cudaError_t e = cudaFuncSetAttribute(
-          decompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-          static_cast<int>(smem));
-      if (e != cudaSuccess) return e;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decompress_kernel,
-                                                        block, smem);
-      if (e != cudaSuccess) return e;
-      int dev = 0;
-      e = cudaGetDevice(&dev);
-      if (e != cudaSuccess) return e;
-      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e != cudaSuccess) return e;
-      cached_block = block;
-    }
-  }
+  static LaunchCache lc;
+  const size_t smem = A.smem_bytes;
+  int per_sm = 0, sms = 0;
+  cudaError_t e = resident_blocks(lc, decompress_kernel, block, smem, &per_sm, &sms);
+  if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   // enough blocks for the largest stream the input could hold, capped at the
   // resident limit (the grid cannot depend on the header: it is on the GPU)

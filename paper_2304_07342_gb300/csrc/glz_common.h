@@ -110,6 +110,54 @@ struct DecItem {
   uint32_t out_aligned;
 };
 
+// Per-warp shared-memory slice of the decoder (byte offsets, 16-byte
+// aligned): an mbarrier, two bitmaps over the chunk's positions (token
+// starts and pointer starts), the high bytes of (offset - 1) when one-byte
+// symbols carry two-byte offsets, then -- when they fit -- the chunk's output
+// and a window for its record.  Without them (`staged` false) a warp
+// decodes straight into the output buffer and reads the record in place.
+struct DecodeLayout {
+  uint32_t bits_off;   // token-start bitmap; the pointer-start bitmap follows
+  uint32_t bit_words;  // 32-bit words per bitmap
+  uint32_t hi_off;     // k bytes (one-byte symbols, two-byte offsets) or none
+  uint32_t out_off;    // C bytes + 16 slack
+  uint32_t win_off;    // largest record + 64 slack
+  uint32_t per_warp;
+  uint32_t staged;
+};
+
+// Largest record of a chunk of k symbols: flags, payload and (stream version
+// 2, last chunk) up to S - 1 tail bytes.
+__host__ __device__ inline uint64_t decode_record_bound(uint64_t k, uint32_t S, uint32_t offB,
+                                                       uint32_t m) {
+  const uint64_t extra = (1u + offB > S * m) ? (1u + offB - S * m) : 0u;
+  return (k + 7) / 8 + static_cast<uint64_t>(S) * k + extra * (k / m) + (S - 1);
+}
+
+// Slice for chunks of at most `kmax` symbols and `cmax` bytes whose records
+// are at most `rmax` bytes; the full slice when `budget` bytes hold it,
+// else the bitmaps alone.
+__host__ __device__ inline DecodeLayout decode_layout(uint64_t kmax, uint64_t cmax,
+                                                      uint64_t rmax, bool hi, uint64_t budget) {
+  DecodeLayout L{};
+  uint64_t at = 16;  // mbarrier
+  L.bits_off = static_cast<uint32_t>(at);
+  L.bit_words = static_cast<uint32_t>((kmax + 31) / 32);
+  at += 8ull * L.bit_words;
+  at = (at + 15) & ~15ull;
+  L.hi_off = static_cast<uint32_t>(at);
+  if (hi) at += (kmax + 15) & ~15ull;
+  const uint64_t base = at;
+  L.out_off = static_cast<uint32_t>(at);
+  at += ((cmax + 15) & ~15ull) + 16;
+  L.win_off = static_cast<uint32_t>(at);
+  at += ((rmax + 15) & ~15ull) + 64;
+  L.staged = at <= budget;
+  if (!L.staged) at = base;
+  L.per_warp = static_cast<uint32_t>(at);
+  return L;
+}
+
 struct DecompressBatchArgs {
   const DecItem *items;        // streams with at least one chunk
   const uint64_t *item_base;   // items[i].gbase, ascending
@@ -117,8 +165,7 @@ struct DecompressBatchArgs {
   uint64_t total_chunks;
   const DecItem *empties;      // streams of zero bytes
   uint32_t n_empty;
-  uint32_t ring_n;             // ring entries per warp (>= W + 32 for every stream)
-  uint32_t win_bytes;          // record window per warp (>= every record + 32)
+  DecodeLayout lay;            // per-warp slice covering every stream
   uint32_t smem_bytes;         // dynamic shared memory per block
   uint32_t *err;
 };

@@ -86,7 +86,7 @@ namespace {
 
 constexpr int kCompressWarps = 4;      // warps per block (fewer if smem-bound)
 constexpr uint32_t kParkSlots = 3;     // parked records per compressing warp
-constexpr int kDecompressBlock = 256;  // 8 warps, one chunk per warp
+constexpr int kDecompressBlock = 1024;  // up to 32 warps, one chunk per warp at a time
 constexpr size_t kScratchHead = 16;
 // Chunks per compression launch: the warps take chunks from a 32-bit work
 // counter and each takes one ticket past the last chunk, so the counter must
@@ -149,6 +149,13 @@ lz_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return LZ_OK;
   if (e == cudaErrorMemoryAllocation) return LZ_ERR_NOMEM;
   return LZ_ERR_CUDA;
+}
+
+// Shared memory of one decoding block: one block per SM, all of the SM's
+// shared memory that a block may take.
+uint32_t decode_block_smem(const lz_ctx *ctx) {
+  const int64_t per_sm = static_cast<int64_t>(ctx->smem_per_sm) - ctx->smem_reserved;
+  return static_cast<uint32_t>(std::min<int64_t>(ctx->smem_optin, per_sm));
 }
 
 // Make sure the scratch area holds `bytes`; synchronous when it grows.
@@ -398,6 +405,7 @@ lz_status lz_decompress(lz_ctx *ctx, const void *d_in, uint64_t in_bytes,
   A.out_bytes = reinterpret_cast<unsigned long long *>(d_out_bytes);
   A.err = ctx->d_err;
   A.out_aligned = (reinterpret_cast<uintptr_t>(d_out) % 16) == 0;
+  A.smem_bytes = decode_block_smem(ctx);
   return cuda_status(glz::launch_decompress(A, kDecompressBlock,
                                             reinterpret_cast<cudaStream_t>(stream)));
 }
@@ -571,10 +579,9 @@ extern "C" lz_status lz_compress_noalloc(const void *d_in, uint64_t n_bytes,
   }
   uint64_t grid = div_up(nc, block / 32);
   if (grid > static_cast<uint64_t>(best_blocks) * nd->sms) grid = best_blocks * nd->sms;
-  // the counter and the status words must start at zero; the error word is
-  // cleared by the previous call's report (and starts at zero)
-  if (cudaMemsetAsync(nd->scratch + kNoAllocHead, 0, 8ull * nc, st) != cudaSuccess ||
-      cudaMemsetAsync(nd->scratch, 0, 4, st) != cudaSuccess)
+  // the counter, the error word and the status words start at zero (one
+  // clear, so that an error left by an earlier failed call cannot leak in)
+  if (cudaMemsetAsync(nd->scratch, 0, kNoAllocHead + 8ull * nc, st) != cudaSuccess)
     return LZ_ERR_CUDA;
   glz::CompressArgs A{};
   A.buf.in = static_cast<const uint8_t *>(d_in);
@@ -617,11 +624,23 @@ extern "C" lz_status lz_compress_noalloc(const void *d_in, uint64_t n_bytes,
 // ---------------------------------------------------------------------------
 // Batches: many buffers in one persistent launch.
 
+// Device buffers a batch owns, one slot each; a re-plan (lz_batch_update)
+// reuses a slot when it is large enough.
+enum BatchBuf { kBufScratch, kBufItems, kBufBases, kBufEmpties, kBufIns, kBufInBytes, kBufHdr,
+                kBufCount };
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
 struct lz_batch {
   int decompress = 0;
   int device = 0;
+  int planned = 0;                // 1 once a plan succeeded (runs allowed)
+  uint32_t match = 0, version = 1;  // compression options of every plan
   cudaStream_t stream = nullptr;  // allocations and uploads are ordered on it
-  std::vector<void *> owned;      // device allocations owned by the batch
+  DevBuf bufs[kBufCount];         // device allocations owned by the batch
   // compression
   glz::CompressArgs cargs{};
   const glz::BufDesc *d_empty = nullptr;
@@ -637,21 +656,34 @@ struct lz_batch {
 
 namespace {
 
-// Stream-ordered allocation on the batch's stream (no device-wide sync).
-lz_status batch_alloc(lz_batch *b, size_t bytes, void **p) {
+// Device memory for slot `slot` of at least `bytes`, stream-ordered on the
+// batch's stream (no device-wide sync): the slot's buffer when it is large
+// enough, else a new one (the old one is freed after the work already
+// enqueued on that stream).  A new buffer has room for half as much again,
+// so that a batch re-planned with a few more items keeps its memory.
+lz_status batch_alloc(lz_batch *b, int slot, size_t bytes, void **p) {
   *p = nullptr;
   if (bytes == 0) return LZ_OK;
-  cudaError_t e = cudaMallocAsync(p, bytes, b->stream);
-  if (e != cudaSuccess) return cuda_status(e);
-  b->owned.push_back(*p);
+  DevBuf &d = b->bufs[slot];
+  if (d.cap < bytes) {
+    if (d.p) cudaFreeAsync(d.p, b->stream);
+    d.p = nullptr;
+    d.cap = 0;
+    const size_t want = bytes + bytes / 2;
+    cudaError_t e = cudaMallocAsync(&d.p, want, b->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    d.cap = want;
+  }
+  *p = d.p;
   return LZ_OK;
 }
 
-// Upload a host array (pageable: the call returns once the data is staged).
+// Upload a host array into slot `slot` (pageable: the call returns once the
+// data is staged).
 template <typename T>
-lz_status batch_upload(lz_batch *b, const std::vector<T> &v, const T **dst) {
+lz_status batch_upload(lz_batch *b, int slot, const std::vector<T> &v, const T **dst) {
   void *p = nullptr;
-  lz_status s = batch_alloc(b, v.size() * sizeof(T), &p);
+  lz_status s = batch_alloc(b, slot, v.size() * sizeof(T), &p);
   if (s != LZ_OK) return s;
   if (!v.empty() && cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T),
                                     cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
@@ -768,13 +800,13 @@ lz_status batch_create_compress(lz_ctx *ctx, const lz_batch_item *items, uint32_
   const size_t status_end = kScratchHead + 8ull * total;
   const size_t park_at = (status_end + 255) & ~static_cast<size_t>(255);
   const size_t scratch = park_at + static_cast<size_t>(slot_bytes) * kParkSlots * wpb * grid;
-  lz_status s = batch_alloc(b, scratch, &b->scratch);
+  lz_status s = batch_alloc(b, kBufScratch, scratch, &b->scratch);
   if (s != LZ_OK) return s;
   const glz::BufDesc *d_items = nullptr, *d_empty = nullptr;
   const uint64_t *d_base = nullptr;
-  if ((s = batch_upload(b, descs, &d_items)) != LZ_OK) return s;
-  if ((s = batch_upload(b, bases, &d_base)) != LZ_OK) return s;
-  if ((s = batch_upload(b, empties, &d_empty)) != LZ_OK) return s;
+  if ((s = batch_upload(b, kBufItems, descs, &d_items)) != LZ_OK) return s;
+  if ((s = batch_upload(b, kBufBases, bases, &d_base)) != LZ_OK) return s;
+  if ((s = batch_upload(b, kBufEmpties, empties, &d_empty)) != LZ_OK) return s;
   glz::CompressArgs &A = b->cargs;
   A.items = d_items;
   A.item_base = d_base;
@@ -814,15 +846,20 @@ lz_status batch_create_decompress(lz_ctx *ctx, const lz_batch_item *items, uint3
     ins[i] = static_cast<const uint8_t *>(items[i].d_in);
     in_bytes[i] = items[i].in_bytes;
   }
+  // an item that states its stream's parameters (params.chunk_bytes != 0)
+  // and, in out_cap, its exact decompressed size needs no header read; the
+  // kernel still checks every header against the plan
+  bool read = false;
+  for (uint32_t i = 0; i < n; ++i) read = read || items[i].params.chunk_bytes == 0;
   std::vector<uint8_t> hdr(static_cast<size_t>(n) * 32);
-  {
+  if (read) {
     const uint8_t *const *d_ins = nullptr;
     const uint64_t *d_inb = nullptr;
     lz_status s;
-    if ((s = batch_upload(b, ins, &d_ins)) != LZ_OK) return s;
-    if ((s = batch_upload(b, in_bytes, &d_inb)) != LZ_OK) return s;
+    if ((s = batch_upload(b, kBufIns, ins, &d_ins)) != LZ_OK) return s;
+    if ((s = batch_upload(b, kBufInBytes, in_bytes, &d_inb)) != LZ_OK) return s;
     void *d_hdr = nullptr;
-    if ((s = batch_alloc(b, hdr.size(), &d_hdr)) != LZ_OK) return s;
+    if ((s = batch_alloc(b, kBufHdr, hdr.size(), &d_hdr)) != LZ_OK) return s;
     if (n) {
       glz::gather_headers<<<std::min<uint32_t>(1024, (n * 32 + 255) / 256), 256, 0,
                             b->stream>>>(d_ins, d_inb, n, static_cast<uint8_t *>(d_hdr));
@@ -834,18 +871,29 @@ lz_status batch_create_decompress(lz_ctx *ctx, const lz_batch_item *items, uint3
   }
   std::vector<glz::DecItem> descs, empties;
   std::vector<uint64_t> bases;
-  uint64_t total = 0, max_rec = 0;
-  uint32_t max_w = 1;
+  uint64_t total = 0, max_rec = 0, max_k = 1, max_c = 16;
+  bool need_hi = false;
   for (uint32_t i = 0; i < n; ++i) {
     const uint8_t *h = &hdr[static_cast<size_t>(i) * 32];
-    lz_params p{h[5], static_cast<uint32_t>(header_u(h, 12, 4)),
-                static_cast<uint32_t>(header_u(h, 16, 4)), h[7], h[8]};
-    const uint64_t nn = header_u(h, 24, 8);
-    const uint64_t nc = header_u(h, 20, 4);
-    if (std::memcmp(h, "GLZ1", 4) != 0 || (h[4] != 1 && h[4] != 2) || h[9] > (h[4] == 2 ? 1 : 0) || h[10] || h[11] ||
-        !params_ok(&p) || h[6] != off_bytes(p.window) || (h[4] == 1 && nn % p.symbol_bytes != 0) ||
-        nc != div_up(nn, p.chunk_bytes))
-      return LZ_ERR_CORRUPT;
+    lz_params p;
+    uint64_t nn, nc;
+    if (items[i].params.chunk_bytes != 0) {
+      p = items[i].params;
+      if (!params_ok(&p)) return LZ_ERR_INVALID_ARG;
+      nn = items[i].out_cap;
+      nc = div_up(nn, p.chunk_bytes);
+      if (nc > 0xFFFFFFFFull) return LZ_ERR_INVALID_ARG;
+    } else {
+      p = lz_params{h[5], static_cast<uint32_t>(header_u(h, 12, 4)),
+                    static_cast<uint32_t>(header_u(h, 16, 4)), h[7], h[8]};
+      nn = header_u(h, 24, 8);
+      nc = header_u(h, 20, 4);
+      if (std::memcmp(h, "GLZ1", 4) != 0 || (h[4] != 1 && h[4] != 2) ||
+          h[9] > (h[4] == 2 ? 1 : 0) || h[10] || h[11] || !params_ok(&p) ||
+          h[6] != off_bytes(p.window) || (h[4] == 1 && nn % p.symbol_bytes != 0) ||
+          nc != div_up(nn, p.chunk_bytes))
+        return LZ_ERR_CORRUPT;
+    }
     if (items[i].out_cap < nn || (nn > 0 && !items[i].d_out)) return LZ_ERR_BUFFER_TOO_SMALL;
     glz::DecItem d{};
     d.in = ins[i];
@@ -863,22 +911,23 @@ lz_status batch_create_decompress(lz_ctx *ctx, const lz_batch_item *items, uint3
     descs.push_back(d);
     bases.push_back(total);
     total += nc;
-    max_w = std::max(max_w, p.window);
-    max_rec = std::max(max_rec, record_bound(p.chunk_bytes / p.symbol_bytes, p.symbol_bytes,
-                                             off_bytes(p.window), p.min_match));
+    const uint64_t k = p.chunk_bytes / p.symbol_bytes;
+    max_k = std::max(max_k, k);
+    max_c = std::max<uint64_t>(max_c, p.chunk_bytes);
+    need_hi = need_hi || (p.symbol_bytes == 1 && off_bytes(p.window) == 2);
+    max_rec = std::max(max_rec, glz::decode_record_bound(k, p.symbol_bytes,
+                                                         off_bytes(p.window), p.min_match));
   }
-  uint32_t ring_n = 64;
-  while (ring_n < max_w + 32) ring_n <<= 1;
-  const uint32_t win = round16(max_rec + 32);
-  const uint64_t need = 16 + 4ull * ring_n + win;
-  if (static_cast<int64_t>(need) > ctx->smem_optin) return LZ_ERR_INVALID_ARG;
-  const uint64_t warps = std::min<uint64_t>(8, ctx->smem_optin / need);
+  const uint32_t budget = decode_block_smem(ctx);
+  const glz::DecodeLayout lay = glz::decode_layout(max_k, max_c, max_rec, need_hi, budget);
+  if (lay.per_warp > budget) return LZ_ERR_INVALID_ARG;
+  const uint64_t warps = std::min<uint64_t>(32, budget / lay.per_warp);
   const glz::DecItem *d_items = nullptr, *d_empty = nullptr;
   const uint64_t *d_base = nullptr;
   lz_status s;
-  if ((s = batch_upload(b, descs, &d_items)) != LZ_OK) return s;
-  if ((s = batch_upload(b, bases, &d_base)) != LZ_OK) return s;
-  if ((s = batch_upload(b, empties, &d_empty)) != LZ_OK) return s;
+  if ((s = batch_upload(b, kBufItems, descs, &d_items)) != LZ_OK) return s;
+  if ((s = batch_upload(b, kBufBases, bases, &d_base)) != LZ_OK) return s;
+  if ((s = batch_upload(b, kBufEmpties, empties, &d_empty)) != LZ_OK) return s;
   glz::DecompressBatchArgs &B = b->dargs;
   B.items = d_items;
   B.item_base = d_base;
@@ -886,9 +935,8 @@ lz_status batch_create_decompress(lz_ctx *ctx, const lz_batch_item *items, uint3
   B.total_chunks = total;
   B.empties = d_empty;
   B.n_empty = static_cast<uint32_t>(empties.size());
-  B.ring_n = ring_n;
-  B.win_bytes = win;
-  B.smem_bytes = static_cast<uint32_t>(need * warps);
+  B.lay = lay;
+  B.smem_bytes = static_cast<uint32_t>(lay.per_warp * warps);
   B.err = ctx->d_err;
   b->dblock = static_cast<int>(32 * warps);
   return LZ_OK;
