@@ -225,15 +225,22 @@ typedef struct lz_batch_item {
   void *d_out;           /* output buffer                                   */
   uint64_t out_cap;
   uint64_t *d_out_bytes; /* device uint64, 8-byte aligned: produced size    */
-  lz_params params;      /* compress: this item's parameters; decompress:
-                            ignored (each stream's header is read)          */
+  lz_params params;      /* compress: this item's parameters.  decompress:
+                            all zero, or the stream's parameters (see
+                            lz_batch_create)                                */
 } lz_batch_item;
 
 typedef struct lz_batch lz_batch;
 
 /* Plan a batch of n_items over the host array `items` (decompress != 0: the
- * items are GLZ1 streams to decompress; their headers are read from the
- * device, which synchronises `stream`).  The batch's device memory is
+ * items are GLZ1 streams to decompress).  A decompression item whose
+ * params.chunk_bytes is 0 has its header read from the device, which
+ * synchronises `stream`; an item that states its stream's parameters in
+ * `params` and its exact decompressed size in `out_cap` is planned without
+ * that read (when every item does, the call does not synchronise), and the
+ * kernel checks each header against the plan: a stream whose header
+ * disagrees is not decoded and is reported as LZ_ERR_CORRUPT by lz_sync.
+ * The batch's device memory is
  * allocated stream-ordered on `stream` (cudaMallocAsync) and its descriptors
  * uploaded on it, so no device-wide synchronisation happens; runs must be
  * ordered after this call (same stream, or an event).  Errors are those of
@@ -252,6 +259,18 @@ lz_status lz_batch_create(lz_ctx *ctx, const lz_batch_item *items, uint32_t n_it
 lz_status lz_batch_create_ex(lz_ctx *ctx, const lz_batch_item *items, uint32_t n_items,
                              int decompress, const lz_options *opt, lz_stream_t stream,
                              lz_batch **out);
+
+/* Re-plan a batch for new items of the same direction and options (those
+ * given to lz_batch_create_ex), keeping its device memory where it is large
+ * enough (a re-plan allocates only when the new items need more; every
+ * buffer is allocated with room for half as much again).  The uploads are
+ * ordered on `stream`, which must also order them after the batch's earlier
+ * runs (the same stream, or an event).  Validation and errors as for
+ * lz_batch_create; after a failed update the batch cannot be run until an
+ * update succeeds.  A run captured in a CUDA graph before the update runs
+ * the old plan's launch shape: capture again. */
+lz_status lz_batch_update(lz_ctx *ctx, lz_batch *batch, const lz_batch_item *items,
+                          uint32_t n_items, lz_stream_t stream);
 
 /* Enqueue one run of the batch on `stream`. */
 lz_status lz_batch_run(lz_ctx *ctx, lz_batch *batch, lz_stream_t stream);

@@ -969,22 +969,40 @@ lz_status lz_batch_create_ex(lz_ctx *ctx, const lz_batch_item *items, uint32_t n
   b->decompress = decompress ? 1 : 0;
   b->device = ctx->device;
   b->stream = reinterpret_cast<cudaStream_t>(stream);
-  const uint32_t kmatch = match == LZ_MATCH_PAPER     ? glz::kMatchPaper
-                         : match == LZ_MATCH_OVERLAP ? glz::kMatchOverlap
-                                                     : glz::kMatchExact;
+  b->match = match == LZ_MATCH_PAPER     ? glz::kMatchPaper
+             : match == LZ_MATCH_OVERLAP ? glz::kMatchOverlap
+                                         : glz::kMatchExact;
+  b->version = version;
   lz_status s = decompress ? batch_create_decompress(ctx, items, n_items, b)
-                           : batch_create_compress(ctx, items, n_items, b, kmatch, version);
+                           : batch_create_compress(ctx, items, n_items, b, b->match, version);
   if (s != LZ_OK) {
-    for (void *p : b->owned) cudaFreeAsync(p, b->stream);
+    for (DevBuf &d : b->bufs)
+      if (d.p) cudaFreeAsync(d.p, b->stream);
     delete b;
     return s;
   }
+  b->planned = 1;
   *out = b;
   return LZ_OK;
 }
 
+lz_status lz_batch_update(lz_ctx *ctx, lz_batch *b, const lz_batch_item *items,
+                          uint32_t n_items, lz_stream_t stream) {
+  if (!ctx || !b || b->device != ctx->device || (n_items > 0 && !items))
+    return LZ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
+  b->stream = reinterpret_cast<cudaStream_t>(stream);
+  b->planned = 0;
+  lz_status s = b->decompress ? batch_create_decompress(ctx, items, n_items, b)
+                              : batch_create_compress(ctx, items, n_items, b, b->match,
+                                                      b->version);
+  if (s == LZ_OK) b->planned = 1;
+  return s;
+}
+
 lz_status lz_batch_run(lz_ctx *ctx, lz_batch *b, lz_stream_t stream) {
-  if (!ctx || !b || b->device != ctx->device) return LZ_ERR_INVALID_ARG;
+  if (!ctx || !b || b->device != ctx->device || !b->planned) return LZ_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (b->decompress) {
     if (b->dargs.total_chunks == 0 && b->dargs.n_empty == 0) return LZ_OK;
@@ -1002,7 +1020,8 @@ void lz_batch_destroy(lz_batch *b, lz_stream_t stream) {
   if (!b) return;
   cudaSetDevice(b->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  for (void *p : b->owned) cudaFreeAsync(p, st);
+  for (DevBuf &d : b->bufs)
+    if (d.p) cudaFreeAsync(d.p, st);
   delete b;
 }
 

@@ -36,7 +36,7 @@ _NAMES = {0: "LZ_OK", 1: "LZ_ERR_INVALID_ARG", 2: "LZ_ERR_BUFFER_TOO_SMALL",
 EXPORTS = ("lz_create", "lz_destroy", "lz_status_string", "lz_check_params",
            "lz_compressed_bound", "lz_compress", "lz_compress_ex", "lz_decompressed_size",
            "lz_decompress", "lz_sync", "lz_compress_noalloc", "lz_batch_create",
-           "lz_batch_run", "lz_batch_destroy", "lz_autotune", "lz_stitch", "lz_batch_create_ex",
+           "lz_batch_run", "lz_batch_update", "lz_batch_destroy", "lz_autotune", "lz_stitch", "lz_batch_create_ex",
            "lz_select_params", "lz_huff_bound", "lz_huff_compress",
            "lz_huff_decompressed_size", "lz_huff_decompress")
 
@@ -118,6 +118,8 @@ def load(path: str = LIB_PATH):
     lib.lz_batch_create_ex.argtypes = [vp, ctypes.POINTER(lz_batch_item), ctypes.c_uint32, i32,
                                        ctypes.POINTER(lz_options), vp, ctypes.POINTER(vp)]
     lib.lz_batch_create_ex.restype = i32
+    lib.lz_batch_update.argtypes = [vp, vp, ctypes.POINTER(lz_batch_item), ctypes.c_uint32, vp]
+    lib.lz_batch_update.restype = i32
     lib.lz_batch_run.argtypes = [vp, vp, vp]
     lib.lz_batch_run.restype = i32
     lib.lz_batch_destroy.argtypes = [vp, vp]
@@ -215,12 +217,11 @@ def lz_compress_noalloc(d_in: int, n_bytes: int, p: Params, d_out: int, out_cap:
 def lz_batch_create(ctx: int, items, decompress: bool = False, stream: int = 0,
                     match: int = 0, version: int = 1) -> int:
     """Plan a batch; `items` is a list of (d_in, in_bytes, d_out, out_cap,
-    d_out_bytes, Params-or-None) tuples of raw device pointers.  `match` and
+    d_out_bytes, Params-or-None) tuples of raw device pointers (for a
+    decompression item, Params states the stream's parameters and out_cap
+    its exact size, so that its header need not be read).  `match` and
     `version` apply to every item of a compression batch (lz_batch_create_ex)."""
-    arr = (lz_batch_item * max(1, len(items)))()
-    for i, (din, nin, dout, cap, dnb, p) in enumerate(items):
-        arr[i] = lz_batch_item(din, nin, dout, cap, dnb,
-                               p.c() if p is not None else lz_params(0, 0, 0, 0, 0))
+    arr = _items(items)
     h = ctypes.c_void_p()
     if match == 0 and version == 1:
         _check(load().lz_batch_create(ctx, arr, len(items), 1 if decompress else 0, stream,
@@ -231,6 +232,21 @@ def lz_batch_create(ctx: int, items, decompress: bool = False, stream: int = 0,
                                          ctypes.byref(opt), stream, ctypes.byref(h)),
                "lz_batch_create_ex")
     return h.value
+
+
+def _items(items):
+    arr = (lz_batch_item * max(1, len(items)))()
+    for i, (din, nin, dout, cap, dnb, p) in enumerate(items):
+        arr[i] = lz_batch_item(din, nin, dout, cap, dnb,
+                               p.c() if p is not None else lz_params(0, 0, 0, 0, 0))
+    return arr
+
+
+def lz_batch_update(ctx: int, batch: int, items, stream: int = 0) -> None:
+    """Re-plan `batch` for new items (same direction and options), reusing
+    its device memory where it is large enough."""
+    _check(load().lz_batch_update(ctx, batch, _items(items), len(items), stream),
+           "lz_batch_update")
 
 
 def lz_batch_run(ctx: int, batch: int, stream: int = 0) -> None:
