@@ -17,16 +17,19 @@ data-path collective.
 
 After the timed steps (not part of them) the line gets more sections on
 the same GPU: `stream_version2` -- the same items as stream version 2
-(stored chunks); `paper_matcher` -- the paper's own matcher (section 3.3.2)
+(stored chunks); `compressible` -- inputs with matches: the 1 MiB
+quantization codes of the small configuration, 256 MiB of them and one
+cell per symbol size of the 1 GiB symbol-size sweep, with compress and
+decompress GB/s and HBM fractions; `paper_matcher` -- the paper's own matcher (section 3.3.2)
 beside the exact one on 256 MiB of uint16 quantization codes; `huffman` --
 the paper's use case (section 4.5), Huffman coding after LZSS, on the same
 codes; `batched` --
 10,000 uneven buffers (4 KiB-16 MiB, four
 kinds, about 20 GB) compressed and decompressed by one persistent launch
 under a CUDA graph vs one plain launch per buffer -- and `served` -- a
-Poisson request stream (2000 requests/s, 10 s by default, --served 60 for
-the full trace) under continuous batching vs one launch per request, with
-p50/p99 latency.
+Poisson request stream (2000 requests/s for 60 s, the full trace; --served
+sets the seconds) under continuous batching vs one launch per request, with
+p50/p99 latency, then a load sweep to saturation.
 
 `--impl reference` times the CPU oracle (the plain definition) on a bounded
 sample of the same workload on the host cores.
@@ -301,7 +304,7 @@ def run_gpu(args):
     line = {
         "metric": METRIC,
         "value": round(n_in * world / (comp_ms * 1e-3) / 1e9, 3),
-        "unit": "GB/s (input bytes compressed per second)",
+        "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
@@ -309,7 +312,7 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "u8/u32 symbols (integer/byte path, lossless)",
+        "dtype": DTYPE,
         "data": "synthetic (seeded generators shaped like the paper's workloads)",
         "config": {"workload": args.workload,
                    "items": [dict(label=it["label"], bytes=int(it["d_in"].numel()),
@@ -343,6 +346,8 @@ def run_gpu(args):
         for k in ("d_in", "d_out", "d_dec"):
             it[k] = None
     torch.cuda.empty_cache()
+    if args.compressible:
+        line["compressible"] = _compressible(torch, codec, args, hbm_peak)
     if args.paper_matcher:
         line["paper_matcher"] = _paper_matcher(torch, codec, args)
     if args.huffman:
@@ -354,6 +359,78 @@ def run_gpu(args):
     if args.served > 0:
         line["served"] = _served(torch, codec, args, args.served)
     return line
+
+
+def _time_codec(torch, codec, d, P, reps: int):
+    """Compress and decompress device tensor d with P: (ratio, compress ms,
+    decompress ms, stream bytes), CUDA events over `reps` calls each after a
+    checked round trip."""
+    from paper_2304_07342_gb300 import lz
+    st = torch.cuda.current_stream()
+    n = d.numel()
+    out, nb = codec.compress(d, P)
+    back, bb = codec.decompress(out, n_bytes=n)
+    if codec.sync() != lz.LZ_OK:
+        raise RuntimeError("compress/decompress failed on the device")
+    size = int(nb.item())
+    if not torch.equal(back, d):
+        raise RuntimeError("round trip differs")
+    for _ in range(2):
+        codec.compress(d, P, out=out, out_bytes=nb)
+        codec.decompress(out, n_bytes=n, out=back, out_bytes=bb, in_bytes=size)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(st)
+    for _ in range(reps):
+        codec.compress(d, P, out=out, out_bytes=nb)
+    ev[1].record(st)
+    for _ in range(reps):
+        codec.decompress(out, n_bytes=n, out=back, out_bytes=bb, in_bytes=size)
+    ev[2].record(st)
+    torch.cuda.synchronize()
+    if codec.sync() != lz.LZ_OK:
+        raise RuntimeError("timed compress/decompress failed on the device")
+    return n / size, ev[0].elapsed_time(ev[1]) / reps, ev[1].elapsed_time(ev[2]) / reps, size
+
+
+def _compressible(torch, codec, args, hbm_peak: float):
+    """Workloads with matches, where the parse and the decoder's pointer
+    resolution do the work: the 1 MiB quantization codes of the small
+    configuration (a single launch, bound by launch latency), 256 MiB of
+    the same codes, and one chunk/window cell per symbol size of the
+    symbol-size sweep (1 GiB of first-order Markov codes stored as uint8,
+    uint16 and uint32, C = 4096, W = 128).  Per input: compress and
+    decompress GB/s (input bytes), the ratio, and each kernel's HBM fraction
+    counting the bytes it must move (input + stream)."""
+    from paper_2304_07342_gb300 import lz, synth
+    rows = []
+
+    def run(name, x, P, reps):
+        d = torch.from_numpy(np.ascontiguousarray(x).view(np.uint8).reshape(-1)).cuda()
+        ratio, c_ms, d_ms, size = _time_codec(torch, codec, d, P, reps)
+        n = d.numel()
+        moved = n + size
+        rows.append({"input": name, "bytes": n, "params": dict(zip("SCWmM", (P.S, P.C, P.W, P.m, P.M))),
+                     "ratio": round(ratio, 4),
+                     "compress_gbs": round(n / (c_ms * 1e-3) / 1e9, 2),
+                     "decompress_gbs": round(n / (d_ms * 1e-3) / 1e9, 2),
+                     "compress_hbm_frac": round(moved / (c_ms * 1e-3) / 1e9 / hbm_peak, 4),
+                     "decompress_hbm_frac": round(moved / (d_ms * 1e-3) / 1e9 / hbm_peak, 4)})
+        del d
+        torch.cuda.empty_cache()
+
+    run("uint16 quant codes 1 MiB (small configuration)", synth.workload_small(seed=args.seed),
+        lz.Params(2, 4096, 128, 3, 255), 50)
+    run("uint16 quant codes 256 MiB", synth.quant_codes_laplace(128 << 20, seed=args.seed),
+        lz.Params(2, 4096, 128, 3, 255), 5)
+    chain = synth.markov_codes(1 << 30, seed=args.seed)
+    for S in (1, 2, 4):
+        x = ((chain % 256).astype(np.uint8) if S == 1 else
+             chain[: (1 << 30) // S].astype({2: np.uint16, 4: np.uint32}[S]))
+        run(f"markov u{8 * S} 1 GiB", x, lz.Params(S, 4096, 128, 2 if S == 4 else 3, 255), 3)
+        del x
+    del chain
+    return {"workload": "quant codes (1 MiB, 256 MiB) and 1 GiB Markov codes at S = 1, 2, 4",
+            "peak_gbs": hbm_peak, "points": rows}
 
 
 def _paper_matcher(torch, codec, args, n_sym: int = 128 << 20):
@@ -516,7 +593,9 @@ def _batched(torch, codec, args, n_buffers: int = 10_000):
 
 def _served(torch, codec, args, seconds: float, budget: int = 40 * 10 ** 9):
     """Poisson request stream: continuous batching vs one plain launch per
-    request, same trace, same HBM budget."""
+    request, same trace, same HBM budget.  Then a load sweep: traces of
+    about 6,000 requests at rising arrival rates, each run both ways, to
+    show where one launch per request saturates."""
     from paper_2304_07342_gb300 import serve
     tr = serve.build_trace(torch, codec, rate=2000.0, duration=seconds, seed=args.seed)
     b = serve.run_batched(torch, codec, tr, budget_bytes=budget)
@@ -524,9 +603,21 @@ def _served(torch, codec, args, seconds: float, budget: int = 40 * 10 ** 9):
     p = serve.run_plain(torch, codec, tr, budget_bytes=budget)
     tr = None
     torch.cuda.empty_cache()
-    return {"workload": f"2000 req/s Poisson for {seconds:g} s, 70% compress, "
-                        "lognormal(256 KiB, 1.5) sizes capped at 64 MiB, S in {1,2,4}",
-            "budget_bytes": budget, "batched": b, "plain": p}
+    out = {"workload": f"2000 req/s Poisson for {seconds:g} s, 70% compress, "
+                       "lognormal(256 KiB, 1.5) sizes capped at 64 MiB, S in {1,2,4}",
+           "budget_bytes": budget, "batched": b, "plain": p}
+    if args.served_sweep:
+        sweep = []
+        for rate in (8000.0, 32000.0, 128000.0, 512000.0):
+            trs = serve.build_trace(torch, codec, rate=rate, duration=6000.0 / rate,
+                                    seed=args.seed + 1)
+            sb = serve.run_batched(torch, codec, trs, budget_bytes=budget)
+            sp = serve.run_plain(torch, codec, trs, budget_bytes=budget)
+            sweep.append({"rate": rate, "requests": sb["requests"], "batched": sb, "plain": sp})
+            trs = None
+            torch.cuda.empty_cache()
+        out["load_sweep"] = sweep
+    return out
 
 
 def _version2(codec, items, stream, reps: int = 5):
@@ -700,80 +791,114 @@ def _link_bandwidth(items, pinned_in, pinned_out, streams):
             "note": "pinned copies of the same buffers, no compression"}
 
 
-def _cpu_baseline(args, budget_s: float = 15.0, hosts=None):
-    """The oracle as it stands, one host thread, on a bounded sample (leading
-    whole chunks of each item) of the same workload."""
+UNIT = "GB/s (input bytes compressed per second)"
+DTYPE = "u8/u32 symbols (integer/byte path, lossless)"
+
+
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_pool_rate(items, threads: int) -> float:
+    """Bytes per second of the oracle compressing `items` -- (bytes, Params,
+    chunk) -- on `threads` host threads.  Each item is cut into pieces of
+    whole index superblocks (64 chunks); chunks are independent (section
+    3.3.1), so the pieces are the same work as the whole.  The oracle's
+    ctypes calls release the interpreter lock, so the threads run on
+    separate cores."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    pieces = []
+    for x, p, C in items:
+        step = max(64 * C, (x.size // max(1, 4 * threads)) // (64 * C) * (64 * C))
+        pieces += [(x[o:o + step], p) for o in range(0, x.size, step)]
+    t = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda a: oracle.compress(*a), pieces))
+    return sum(x.size for x, _, _ in items) / (time.perf_counter() - t)
+
+
+def _cpu_sample(args, hosts, budget_s: float, threads: int):
+    """Leading whole chunks of each item of the workload, sized so that the
+    oracle on `threads` threads takes about budget_s seconds in all."""
     import oracle
     oracle.build()
-    t_total, n_total, desc = 0.0, 0, []
-    per_item = budget_s / len(_workloads()[args.workload])
-    for i, (label, gen, P) in enumerate(_workloads()[args.workload]):
+    wl = _workloads()[args.workload]
+    probe = []
+    for i, (label, gen, P) in enumerate(wl):
         x = hosts[i] if hosts is not None else gen(args.seed)
         x = np.ascontiguousarray(x).view(np.uint8).reshape(-1)
-        p = oracle.Params(*P)
-        n = min(x.size, 64 * P[1])
-        t = time.perf_counter()
-        oracle.compress(x[:n], p)
-        dt = time.perf_counter() - t
-        # grow the sample until the budget is used (rate is ~constant per chunk)
-        n2 = int(min(x.size, max(n, n * per_item / max(dt, 1e-6) * 0.8)))
-        n2 -= n2 % P[1]
-        if n2 > n:
-            t = time.perf_counter()
-            oracle.compress(x[:n2], p)
-            dt = time.perf_counter() - t
-            n = n2
-        t_total += dt
-        n_total += n
-        desc.append(f"{label}: first {n} bytes")
-    return {"value": round(n_total / t_total / 1e9, 6), "unit": "GB/s", "cores": 1,
-            "kind": "oracle", "sample": "; ".join(desc)}
+        probe.append((label, x, oracle.Params(*P), P[1]))
+    # rate from a small sample (64 chunks per thread of every item)
+    small = [(x[: min(x.size, 64 * C * threads)], p, C) for _, x, p, C in probe]
+    rate = _oracle_pool_rate(small, threads)
+    per_item = max(64 * max(C for *_, C in probe), int(rate * budget_s / len(probe)))
+    sample = []
+    for label, x, p, C in probe:
+        n = min(x.size, max(C, per_item - per_item % (64 * C)))
+        sample.append((label, x[:n], p, C))
+    return sample
+
+
+def _cpu_baseline(args, budget_s: float = 15.0, hosts=None):
+    """The oracle as it stands on the host cores, on a bounded sample (leading
+    whole chunks of each item) of the same workload: all cores (the value)
+    and one core."""
+    threads = os.cpu_count() or 1
+    sample = _cpu_sample(args, hosts, budget_s, threads)
+    items = [(x, p, C) for _, x, p, C in sample]
+    value = _oracle_pool_rate(items, threads)
+    one = [(x[: max(C, x.size // threads // C * C)], p, C) for x, p, C in items]
+    single = _oracle_pool_rate(one, 1)
+    return {"value": round(value / 1e9, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "single_core_value": round(single / 1e9, 6), "cpu_model": _cpu_model(),
+            "sample": "; ".join(f"{label}: first {x.size} bytes" for label, x, _, _ in sample) +
+                      f" (one core: the first 1/{threads} of each)"}
 
 
 def run_reference(args):
-    """The reference arm: the oracle as it stands, one host thread, W warm-up
-    and K timed steps, each step compressing the same bounded sample (the
-    leading whole chunks of every item of the workload).  The warm-up steps
-    size the sample so that a step takes about 60 s / (K + W), between 0.2 s
-    and 5 s."""
+    """The reference arm: the oracle as it stands on all host cores (one
+    thread per core over superblock-aligned pieces), W warm-up and K timed
+    steps, each step compressing the same bounded sample (the leading whole
+    chunks of every item of the workload), sized so that the whole run takes
+    about a minute."""
     rank, world, local = _dist()
     if rank != 0:
         return None
-    import oracle
-    oracle.build()
+    threads = os.cpu_count() or 1
     step_s = min(5.0, max(0.2, 60.0 / max(1, args.steps + args.warmup)))
-    items = []
-    for label, gen, P in _workloads()[args.workload]:
-        x = np.ascontiguousarray(gen(args.seed)).view(np.uint8).reshape(-1)
-        items.append([label, x, oracle.Params(*P), P[1], min(x.size, 16 * P[1])])
-    per_item = step_s / len(items)
+    sample = _cpu_sample(args, None, step_s, threads)
+    items = [(x, p, C) for _, x, p, C in sample]
     for _ in range(max(1, args.warmup)):
-        for it in items:
-            label, x, p, C, n = it
-            t = time.perf_counter()
-            oracle.compress(x[:n], p)
-            dt = time.perf_counter() - t
-            n2 = int(n * per_item / max(dt, 1e-6))
-            it[4] = min(x.size, max(C, n2 - n2 % C))
+        _oracle_pool_rate(items, threads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        for label, x, p, C, n in items:
-            oracle.compress(x[:n], p)
+        _oracle_pool_rate(items, threads)
     dt = time.perf_counter() - t0
-    step_bytes = sum(it[4] for it in items)
+    step_bytes = sum(x.size for x, _, _ in items)
     value = round(args.steps * step_bytes / dt / 1e9, 6)
-    cb = {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-          "sample": "; ".join(f"{it[0]}: first {it[4]} bytes" for it in items) +
+    cb = {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+          "cpu_model": _cpu_model(),
+          "sample": "; ".join(f"{label}: first {x.size} bytes" for label, x, _, _ in sample) +
                     f" (every step; {args.steps} timed steps of {dt / max(1, args.steps):.3f} s)"}
     return {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / max(1, args.steps) * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u8/u32 symbols", "data": "synthetic",
+        "dtype": DTYPE, "data": "synthetic (seeded generators shaped like the paper's workloads)",
         "config": {"workload": args.workload},
         "cpu_baseline": cb,
-        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
 
@@ -793,12 +918,17 @@ def main():
                     help="also run the 1 GiB symbol-size sweep (S x chunk x window)")
     ap.add_argument("--no-huffman", dest="huffman", action="store_false",
                     help="skip the LZSS-then-Huffman use case")
+    ap.add_argument("--no-compressible", dest="compressible", action="store_false",
+                    help="skip the compressible workloads (small configuration, quant codes, "
+                         "one sweep cell per symbol size)")
     ap.add_argument("--no-paper-matcher", dest="paper_matcher", action="store_false",
                     help="skip the exact-vs-paper matcher comparison")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 10,000-buffer batched comparison")
-    ap.add_argument("--served", type=float, default=10.0,
-                    help="seconds of the serving trace (0 skips it; the full trace is 60)")
+    ap.add_argument("--served", type=float, default=60.0,
+                    help="seconds of the serving trace (the full trace is 60; 0 skips it)")
+    ap.add_argument("--no-served-sweep", dest="served_sweep", action="store_false",
+                    help="skip the serving load sweep")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

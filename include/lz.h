@@ -342,6 +342,34 @@ lz_status lz_stitch(lz_ctx *ctx, const void *d_shard, uint64_t shard_bytes,
  * returned: INTERNAL, TIMEOUT, CORRUPT, then BUFFER_TOO_SMALL. */
 lz_status lz_sync(lz_ctx *ctx, lz_stream_t stream);
 
+/* ---- Test hooks --------------------------------------------------------------
+ * For tests of the error paths only (no paper counterpart): they make a
+ * bounded device wait run out, or an allocation fail, on purpose, without
+ * faulting or hanging a GPU.  All zero (the state of a new context) means
+ * normal operation; hooks == NULL resets them.  They apply to the context's
+ * later calls:
+ *   spin_limit  polls before a compression kernel's device waits give up
+ *               (look-back and TMA staging; 0: the library's limit, about
+ *               four million polls with back-off up to 1 us between
+ *               look-back polls).  A wait that gives up raises
+ *               LZ_ERR_TIMEOUT (returned by lz_sync) and the kernel
+ *               finishes; the stream written is then incomplete.
+ *   first_chunk lz_compress / lz_compress_ex hand out chunks from this one
+ *               on, so chunks before it are never compressed and the
+ *               look-back of the chunks after them waits for a prefix that
+ *               never comes (with a small spin_limit: LZ_ERR_TIMEOUT).
+ *   fail_alloc  when nonzero, every device allocation the context (or a
+ *               batch planned on it) would make fails with LZ_ERR_NOMEM
+ *               before anything is enqueued; memory already held is used.
+ * LZ_ERR_INVALID_ARG for ctx == NULL. */
+typedef struct lz_test_hooks {
+  uint32_t spin_limit;
+  uint32_t first_chunk;
+  uint32_t fail_alloc;
+} lz_test_hooks;
+
+lz_status lz_set_test_hooks(lz_ctx *ctx, const lz_test_hooks *hooks);
+
 /* ---- Huffman stage ----------------------------------------------------------
  * In the paper's use case (section 4.5) gpuLZ runs before cuSZ's Huffman
  * encoding.  The paper does not print that stage, so its definition here is

@@ -775,16 +775,17 @@ __device__ __forceinline__ bool lookback_try(const unsigned long long *status,
   return false;
 }
 
-// Blocking look-back: retry with exponential back-off; after kSpinLimit
+// Blocking look-back: retry with exponential back-off; after `limit`
 // attempts give up, raise kErrTimeout and return false.  Each attempt scans
 // back as far as needed: every chunk publishes its aggregate as soon as its
 // parse is done, so a full scan only ever waits on chunks still parsing, and
 // chunk 0 always holds a prefix.
 __device__ __forceinline__ bool lookback_wait(const unsigned long long *status,
                                               uint32_t c, uint32_t lane,
-                                              uint32_t *err, uint64_t &excl) {
+                                              uint32_t *err, uint64_t &excl,
+                                              uint32_t limit) {
   uint32_t nap = 32;
-  for (uint32_t spins = 0; spins < kSpinLimit; ++spins) {
+  for (uint32_t spins = 0; spins < limit; ++spins) {
     if (lookback_try(status, c, lane, excl, 0xFFFFFFFFu)) return true;
     __nanosleep(nap);
     nap = min(nap * 2, 1024u);
@@ -863,7 +864,7 @@ __device__ __forceinline__ void drain_parked(const CompressArgs &A, WarpState &W
     bool data_ok = true;
     if (!ok && wait) {
       ok = true;
-      data_ok = lookback_wait(A.status + B.gbase, cs, lane, A.err, excl);
+      data_ok = lookback_wait(A.status + B.gbase, cs, lane, A.err, excl, A.spin_limit);
     }
     if (!ok) continue;
     if (rs & kLiteralRef) {
@@ -960,7 +961,7 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
   for (uint32_t i = bulk + lane; i < bytes; i += 32) W.inb[i] = src[i];
   bool staged = true;
   if (bulk) {
-    staged = mbar_wait_bounded(W.bar, W.phase);
+    staged = mbar_wait_bounded(W.bar, W.phase, A.spin_limit);
     W.phase ^= 1u;
     if (!staged && lane == 0) atomicOr(A.err, kErrTimeout);
   }
@@ -1054,7 +1055,7 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
         W.slot_rec = static_cast<uint32_t>(rec) | (by_ref ? kLiteralRef : 0u);
       }
     } else {
-      const bool ok = lookback_wait(status, c, lane, A.err, excl);
+      const bool ok = lookback_wait(status, c, lane, A.err, excl, A.spin_limit);
       place_record(A, B, c, excl, rec, W.flags, fb, payload, pb, data_ok && ok, lane);
     }
   }
@@ -1062,9 +1063,9 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
   return staged;
 }
 
-__device__ __forceinline__ uint32_t take_ticket(uint32_t *ticket, uint32_t lane) {
+__device__ __forceinline__ uint32_t take_ticket(const CompressArgs &A, uint32_t lane) {
   uint32_t t = 0;
-  if (lane == 0) t = atomicAdd(ticket, 1u);
+  if (lane == 0) t = atomicAdd(A.ticket, 1u) + A.first_ticket;
   return __shfl_sync(kFull, t, 0);
 }
 
@@ -1076,7 +1077,7 @@ __global__ void __launch_bounds__(256) compress_kernel(const CompressArgs A) {
   WarpState W;
   init_warp_state(A, smem, W, lane);
   while (true) {
-    const uint32_t c = take_ticket(A.ticket, lane);
+    const uint32_t c = take_ticket(A, lane);
     if (c >= A.buf.nc) break;
     // one-byte links exactly when W <= 256, which is when NJ <= 8
     if (!compress_chunk<S, NJ, (NJ > 8)>(A, A.buf, 0, c, W, lane)) break;
@@ -1110,7 +1111,7 @@ __global__ void __launch_bounds__(256) compress_batch_kernel(const CompressArgs 
   WarpState W;
   init_warp_state(A, smem, W, lane);
   while (true) {
-    const uint32_t g = take_ticket(A.ticket, lane);
+    const uint32_t g = take_ticket(A, lane);
     if (g >= A.total_chunks) break;
     const uint32_t item = find_item(A, g, lane);
     const BufDesc B = A.items[item];

@@ -206,6 +206,24 @@ __device__ __forceinline__ Slice make_slice(uint8_t *ws, const DecodeLayout &L, 
   return sl;
 }
 
+// Flag word g of a record (tokens 32g .. 32g+31; bits of tokens past ntok
+// cleared).  STAGED: the flags are in shared memory, where a word may be
+// read past the flag bytes.
+template <bool STAGED>
+__device__ __forceinline__ uint32_t flag_word(const uint8_t *flags, uint32_t g, uint32_t ntok,
+                                              uint32_t fb) {
+  uint32_t fw;
+  if constexpr (STAGED) {
+    fw = ld_u32_any(flags + 4 * g);
+  } else {
+    fw = 0;
+    for (uint32_t i = 0; i < 4; ++i)
+      if (4 * g + i < fb) fw |= static_cast<uint32_t>(flags[4 * g + i]) << (8 * i);
+  }
+  const uint32_t left = ntok - 32 * g;
+  return left >= 32 ? fw : fw & ((1u << left) - 1u);
+}
+
 // Phases 1 and 2 for a chunk of k symbols with ntok tokens whose payload
 // holds pay_tok bytes of tokens: the symbols are written into `ob` (the
 // output image, or the output itself).  STAGED: the record is in shared
@@ -229,65 +247,89 @@ __device__ __forceinline__ bool decode_tokens(const Header &h, const uint8_t *fl
   }
   __syncwarp();
 
-  // Phase 1: tokens, 32 at a time (lane = token)
-  uint32_t pos = 0, payu = 0;
-  for (uint32_t tb = 0; tb < ntok; tb += 32) {
-    const uint32_t nv = min(32u, ntok - tb);
-    const uint32_t vm = nv == 32 ? kFull : ((1u << nv) - 1u);
-    uint32_t fw;
-    if constexpr (STAGED) {
-      fw = ld_u32_any(flags + (tb >> 3));
-    } else {
-      fw = 0;
-      for (uint32_t i = 0; i < 4; ++i)
-        if ((tb >> 3) + i < fb) fw |= static_cast<uint32_t>(flags[(tb >> 3) + i]) << (8 * i);
-    }
-    fw &= vm;
-    const uint32_t nm = __popc(fw);
-    const uint32_t gpay = S * (nv - nm) + tsz * nm;
-    if (payu + gpay > pay_tok) return false;
-    const bool valid = lane < nv;
-    const bool ism = (fw >> lane) & 1u;
-    const uint32_t nmb = __popc(fw & lt);
-    const uint32_t my_off = payu + S * (lane - nmb) + tsz * nmb;
-    uint32_t w = 0;
-    if (valid) {
-      if constexpr (STAGED) w = ld_u32_any(payload + my_off);
-      else w = static_cast<uint32_t>(ld_le(payload + my_off, ism ? tsz : S));
-    }
-    const uint32_t len = ism ? (w & 0xFFu) : (valid ? 1u : 0u);
-    const uint32_t off = ism ? ((w >> 8) & offmask) + 1u : 0u;
-    uint32_t x = len;  // inclusive scan of token lengths
+  // Phase 1: tokens (lane = token), two groups of 32 per step.  The flag
+  // words are read 32 at a time (lane = group); a scan of their popcounts
+  // gives every group the pointers before it, so each token's payload
+  // offset follows without a running sum: S bytes per literal and 1 + offB
+  // per pointer before it.  The payload must hold exactly the flagged
+  // tokens, checked before any token is read.
+  const uint32_t ngroups = (ntok + 31) / 32;
+  uint32_t np = 0;
+  for (uint32_t g = lane; g < ngroups; g += 32)
+    np += __popc(flag_word<STAGED>(flags, g, ntok, fb));
+  np = __reduce_add_sync(kFull, np);
+  if (S * (ntok - np) + tsz * np != pay_tok) return false;
+  auto put = [&](uint32_t st, bool m, uint32_t off, uint32_t w) {
+    const uint32_t bit = 1u << (st & 31u);
+    atomicOr(&sbits[st >> 5], bit);
+    if (m) atomicOr(&mbits[st >> 5], bit);
+    st_slot<S>(ob, st, m ? off - 1u : w, aligned);
+    if (S == 1 && sl.hi && m) sl.hi[st] = static_cast<uint8_t>((off - 1u) >> 8);
+  };
+  uint32_t pos = 0, pdone = 0;  // symbols produced; pointers in earlier blocks of groups
+  for (uint32_t g0 = 0; g0 < ngroups; g0 += 32) {
+    const uint32_t fwr = g0 + lane < ngroups ? flag_word<STAGED>(flags, g0 + lane, ntok, fb) : 0u;
+    const uint32_t cnt = __popc(fwr);
+    uint32_t incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, x, o);
-      if (lane >= static_cast<uint32_t>(o)) x += y;
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= static_cast<uint32_t>(o)) incl += y;
     }
-    const uint32_t glen = __shfl_sync(kFull, x, 31);
-    const uint32_t start = pos + x - len;
-    const bool tbad = ism && (len == 0 || off > h.W || (len > off && !h.overlap) || off > start);
-    if (__any_sync(kFull, tbad) || pos + glen > k) return false;
-    if (valid) {
-      const uint32_t bit = 1u << (start & 31u);
-      atomicOr(&sbits[start >> 5], bit);
-      if (ism) {
-        atomicOr(&mbits[start >> 5], bit);
-        st_slot<S>(ob, start, off - 1u, aligned);
-        if (S == 1 && sl.hi) sl.hi[start] = static_cast<uint8_t>((off - 1u) >> 8);
+    const uint32_t pb = pdone + incl - cnt;  // pointers before group g0 + lane
+    pdone += __shfl_sync(kFull, incl, 31);
+    const uint32_t nblk = min(32u, ngroups - g0);
+    for (uint32_t i = 0; i < nblk; i += 2) {
+      const bool hasB = i + 1 < nblk;
+      const uint32_t fwA = __shfl_sync(kFull, fwr, i), pbA = __shfl_sync(kFull, pb, i);
+      const uint32_t fwB = __shfl_sync(kFull, fwr, (i + 1) & 31u);
+      const uint32_t pbB = __shfl_sync(kFull, pb, (i + 1) & 31u);
+      const uint32_t tA = (g0 + i) * 32 + lane, tB = tA + 32;
+      const bool vA = tA < ntok, vB = hasB && tB < ntok;
+      const bool mA = (fwA >> lane) & 1u, mB = hasB && ((fwB >> lane) & 1u);
+      const uint32_t nbA = pbA + __popc(fwA & lt), nbB = pbB + __popc(fwB & lt);
+      const uint32_t oA = S * (tA - nbA) + tsz * nbA, oB = S * (tB - nbB) + tsz * nbB;
+      uint32_t wA = 0, wB = 0;
+      if constexpr (STAGED) {
+        if (vA) wA = ld_u32_any(payload + oA);
+        if (vB) wB = ld_u32_any(payload + oB);
       } else {
-        st_slot<S>(ob, start, w, aligned);
+        if (vA) wA = static_cast<uint32_t>(ld_le(payload + oA, mA ? tsz : S));
+        if (vB) wB = static_cast<uint32_t>(ld_le(payload + oB, mB ? tsz : S));
       }
+      const uint32_t lenA = mA ? (wA & 0xFFu) : (vA ? 1u : 0u);
+      const uint32_t lenB = mB ? (wB & 0xFFu) : (vB ? 1u : 0u);
+      const uint32_t offA = mA ? ((wA >> 8) & offmask) + 1u : 0u;
+      const uint32_t offB = mB ? ((wB >> 8) & offmask) + 1u : 0u;
+      uint32_t xA = lenA, xB = lenB;  // inclusive scans of token lengths
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t yA = __shfl_up_sync(kFull, xA, o);
+        const uint32_t yB = __shfl_up_sync(kFull, xB, o);
+        if (lane >= static_cast<uint32_t>(o)) {
+          xA += yA;
+          xB += yB;
+        }
+      }
+      const uint32_t glA = __shfl_sync(kFull, xA, 31), glB = __shfl_sync(kFull, xB, 31);
+      const uint32_t sA = pos + xA - lenA, sB = pos + glA + xB - lenB;
+      // a pointer needs 1 <= length <= offset (any length <= 255 in overlap
+      // mode) and offset <= min(W, its start): its source lies in the chunk
+      const uint32_t capA = h.overlap ? 256u : offA, capB = h.overlap ? 256u : offB;
+      const bool bad = (mA && !(lenA - 1u < capA && offA <= min(h.W, sA))) ||
+                       (mB && !(lenB - 1u < capB && offB <= min(h.W, sB)));
+      if (__any_sync(kFull, bad) || pos + glA + glB > k) return false;
+      pos += glA + glB;
+      if (vA) put(sA, mA, offA, wA);
+      if (vB) put(sB, mB, offB, wB);
     }
-    pos += glen;
-    payu += gpay;
   }
-  if (pos != k || payu != pay_tok) return false;
+  if (pos != k) return false;
   __syncwarp();
 
   // Phase 2: positions, 32 at a time (lane = position)
   const uint32_t le = lt | (1u << lane);
-  bool cm = false;    // the token owning the previous round's last position is a pointer
-  uint32_t coff = 0;  // and its offset
+  uint32_t carry = 0;  // offset of the pointer owning the previous round's last position (0: literal)
   for (uint32_t r0 = 0; r0 < k; r0 += 32) {
     const uint32_t j = r0 + lane;
     const bool act = j < k;
@@ -297,12 +339,10 @@ __device__ __forceinline__ bool decode_tokens(const Header &h, const uint8_t *fl
     const uint32_t mb = sw & le;
     const uint32_t ol = (31u - __clz(mb)) & 31u;  // owner's lane when mb != 0
     const uint32_t oraw = __shfl_sync(kFull, raw, ol);
-    const bool om = mb ? ((mw >> ol) & 1u) != 0 : cm;
-    const uint32_t off = mb ? oraw + 1u : coff;
-    cm = __shfl_sync(kFull, om ? 1u : 0u, 31) != 0;
-    coff = __shfl_sync(kFull, off, 31);
-    const bool ptr = act && om;
-    uint32_t f = ptr ? j - off : j;
+    const uint32_t own = mb ? (((mw >> ol) & 1u) ? oraw + 1u : 0u) : carry;
+    carry = __shfl_sync(kFull, own, 31);
+    const bool ptr = act && own != 0;
+    uint32_t f = ptr ? j - own : j;
     if (__any_sync(kFull, ptr && f >= r0)) {
       // sources inside this round: jump until every source is a literal of
       // the round or lies before it (chains shrink, so at most 5 rounds)
@@ -549,10 +589,6 @@ __global__ void __launch_bounds__(1024, 1) decompress_batch_kernel(const Decompr
     if (!decode_chunk(A, h, c, records_at, base, lane)) break;
   }
 }
-
-// Warps per decoding block: one block per SM holds as many warp slices as
-// its shared memory allows.
-constexpr int kDecodeBlock = 1024;
 
 cudaError_t launch_decompress_batch(DecompressBatchArgs B, int block, cudaStream_t stream) {
   static LaunchCache lc;

@@ -80,6 +80,7 @@ struct lz_ctx {
   size_t scratch_bytes = 0;
   uint32_t *d_err = nullptr;
   std::mutex mu;
+  lz_test_hooks hooks{};    // test hooks (lz_set_test_hooks); all zero normally
 };
 
 namespace {
@@ -161,6 +162,7 @@ uint32_t decode_block_smem(const lz_ctx *ctx) {
 // Make sure the scratch area holds `bytes`; synchronous when it grows.
 lz_status reserve_scratch(lz_ctx *ctx, size_t bytes) {
   if (ctx->scratch_bytes >= bytes) return LZ_OK;
+  if (ctx->hooks.fail_alloc) return LZ_ERR_NOMEM;  // injected failure (test hook)
   size_t want = ctx->scratch_bytes ? ctx->scratch_bytes : (1u << 16);
   while (want < bytes) want *= 2;
   if (ctx->scratch) {
@@ -193,6 +195,13 @@ const char *lz_status_string(lz_status s) {
     case LZ_ERR_INTERNAL: return "LZ_ERR_INTERNAL";
   }
   return "LZ_ERR_UNKNOWN";
+}
+
+lz_status lz_set_test_hooks(lz_ctx *ctx, const lz_test_hooks *hooks) {
+  if (!ctx) return LZ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  ctx->hooks = hooks ? *hooks : lz_test_hooks{};
+  return LZ_OK;
 }
 
 lz_status lz_check_params(const lz_params *p) {
@@ -353,6 +362,8 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
   A.status = reinterpret_cast<unsigned long long *>(
       static_cast<uint8_t *>(ctx->scratch) + kScratchHead);
   A.err = ctx->d_err;
+  A.spin_limit = ctx->hooks.spin_limit ? ctx->hooks.spin_limit : glz::kSpinLimit;
+  A.first_ticket = ctx->hooks.first_chunk;
   uint32_t nj = 1;
   while (32 * nj < p->window) nj *= 2;
   const unsigned g = static_cast<unsigned>(grid);
@@ -606,6 +617,7 @@ extern "C" lz_status lz_compress_noalloc(const void *d_in, uint64_t n_bytes,
   A.park_slot_bytes = 0;
   A.ticket = reinterpret_cast<uint32_t *>(nd->scratch);
   A.err = reinterpret_cast<uint32_t *>(nd->scratch + 4);
+  A.spin_limit = glz::kSpinLimit;
   A.status = reinterpret_cast<unsigned long long *>(nd->scratch + kNoAllocHead);
   uint32_t nj = 1;
   while (32 * nj < p->window) nj *= 2;
@@ -638,6 +650,7 @@ struct lz_batch {
   int decompress = 0;
   int device = 0;
   int planned = 0;                // 1 once a plan succeeded (runs allowed)
+  int fail_alloc = 0;             // the context's injected allocation failure (test hook)
   uint32_t match = 0, version = 1;  // compression options of every plan
   cudaStream_t stream = nullptr;  // allocations and uploads are ordered on it
   DevBuf bufs[kBufCount];         // device allocations owned by the batch
@@ -666,6 +679,7 @@ lz_status batch_alloc(lz_batch *b, int slot, size_t bytes, void **p) {
   if (bytes == 0) return LZ_OK;
   DevBuf &d = b->bufs[slot];
   if (d.cap < bytes) {
+    if (b->fail_alloc) return LZ_ERR_NOMEM;  // injected failure (test hook)
     if (d.p) cudaFreeAsync(d.p, b->stream);
     d.p = nullptr;
     d.cap = 0;
@@ -820,6 +834,8 @@ lz_status batch_create_compress(lz_ctx *ctx, const lz_batch_item *items, uint32_
   A.park = static_cast<uint8_t *>(b->scratch) + park_at;
   A.park_slots = kParkSlots;
   A.park_slot_bytes = slot_bytes;
+  A.spin_limit = glz::kSpinLimit;
+  A.first_ticket = 0;
   b->d_empty = d_empty;
   b->n_empty = static_cast<uint32_t>(empties.size());
   b->nj = nj;
@@ -966,6 +982,7 @@ lz_status lz_batch_create_ex(lz_ctx *ctx, const lz_batch_item *items, uint32_t n
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
   lz_batch *b = new (std::nothrow) lz_batch();
   if (!b) return LZ_ERR_NOMEM;
+  b->fail_alloc = ctx->hooks.fail_alloc ? 1 : 0;
   b->decompress = decompress ? 1 : 0;
   b->device = ctx->device;
   b->stream = reinterpret_cast<cudaStream_t>(stream);
@@ -993,6 +1010,7 @@ lz_status lz_batch_update(lz_ctx *ctx, lz_batch *b, const lz_batch_item *items,
   std::lock_guard<std::mutex> lock(ctx->mu);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
   b->stream = reinterpret_cast<cudaStream_t>(stream);
+  b->fail_alloc = ctx->hooks.fail_alloc ? 1 : 0;
   b->planned = 0;
   lz_status s = b->decompress ? batch_create_decompress(ctx, items, n_items, b)
                               : batch_create_compress(ctx, items, n_items, b, b->match,

@@ -38,7 +38,7 @@ EXPORTS = ("lz_create", "lz_destroy", "lz_status_string", "lz_check_params",
            "lz_decompress", "lz_sync", "lz_compress_noalloc", "lz_batch_create",
            "lz_batch_run", "lz_batch_update", "lz_batch_destroy", "lz_autotune", "lz_stitch", "lz_batch_create_ex",
            "lz_select_params", "lz_huff_bound", "lz_huff_compress",
-           "lz_huff_decompressed_size", "lz_huff_decompress")
+           "lz_huff_decompressed_size", "lz_huff_decompress", "lz_set_test_hooks")
 
 
 class LzError(RuntimeError):
@@ -55,6 +55,11 @@ class lz_params(ctypes.Structure):
 
 class lz_options(ctypes.Structure):
     _fields_ = [("match", ctypes.c_uint32), ("version", ctypes.c_uint32)]
+
+
+class lz_test_hooks(ctypes.Structure):
+    _fields_ = [("spin_limit", ctypes.c_uint32), ("first_chunk", ctypes.c_uint32),
+                ("fail_alloc", ctypes.c_uint32)]
 
 
 class lz_batch_item(ctypes.Structure):
@@ -137,6 +142,8 @@ def load(path: str = LIB_PATH):
     lib.lz_huff_decompressed_size.restype = i32
     lib.lz_huff_decompress.argtypes = [vp, vp, u64, vp, u64, vp, vp]
     lib.lz_huff_decompress.restype = i32
+    lib.lz_set_test_hooks.argtypes = [vp, ctypes.POINTER(lz_test_hooks)]
+    lib.lz_set_test_hooks.restype = i32
     lib.lz_stitch.argtypes = [vp, vp, u64, u64, u64, u64, u64, u64, vp, u64, vp]
     lib.lz_stitch.restype = i32
     _lib = lib
@@ -295,6 +302,13 @@ def lz_huff_decompress(ctx: int, d_in: int, in_bytes: int, d_out: int, out_cap: 
                        d_out_bytes: int, stream: int = 0) -> None:
     _check(load().lz_huff_decompress(ctx, d_in, in_bytes, d_out, out_cap, d_out_bytes, stream),
            "lz_huff_decompress")
+
+
+def lz_set_test_hooks(ctx: int, spin_limit: int = 0, first_chunk: int = 0,
+                      fail_alloc: int = 0) -> None:
+    """Test hooks of a context (all zero: normal operation); see lz.h."""
+    h = lz_test_hooks(spin_limit, first_chunk, fail_alloc)
+    _check(load().lz_set_test_hooks(ctx, ctypes.byref(h)), "lz_set_test_hooks")
 
 
 def lz_sync(ctx: int, stream: int = 0) -> int:

@@ -6,10 +6,12 @@ resident input slices.  The loop:
 
 * admits queued requests in arrival order while their output space fits a
   stated HBM budget (a first-fit allocator over one preallocated buffer);
-* runs every admitted group as one batch (``lz_batch_create`` +
-  ``lz_batch_run``: one persistent launch per direction) on one of a few
-  streams, so groups admitted while others are still on the GPU overlap with
-  them;
+* runs every admitted group as one batch per direction (one persistent
+  launch each) on one of a few streams, so groups admitted while others are
+  still on the GPU overlap with them.  Each stream keeps its two batches and
+  re-plans them for every group (``lz_batch_update``: descriptors uploaded
+  into the batch's own device memory); decompression items state their
+  stream's parameters and size, so no plan waits on the GPU;
 * takes completion times from CUDA events (GPU clock, same origin as the
   arrival clock), hands each finished request to an optional callback and
   then frees its output space.
@@ -36,11 +38,12 @@ class Request:
     compress: bool
     d_in: int               # device pointer
     n_in: int
-    params: object          # lz.Params for compress
-    n_out_max: int          # output capacity needed
+    params: object          # lz.Params (compress: to use; decompress: the stream's)
+    n_out_max: int          # output capacity needed (decompress: the exact size)
     n_orig: int             # uncompressed size
     out_off: int = -1       # arena offset once admitted
     done: float = -1.0
+    source: object = None   # device view of the uncompressed bytes
 
 
 class Arena:
@@ -108,12 +111,22 @@ def build_trace(torch, codec, rate=2000.0, duration=60.0, seed=0, pool_bytes=256
         P = params[S]
         if comp[i]:
             reqs.append(Request(i, float(t[i]), True, view.data_ptr(), n, P,
-                                lz.lz_compressed_bound(n, P), n))
+                                lz.lz_compressed_bound(n, P), n, source=view))
         else:
             s = codec.compress_sync(view, P)
             keep.append(s)
-            reqs.append(Request(i, float(t[i]), False, s.data_ptr(), s.numel(), None, n, n))
+            reqs.append(Request(i, float(t[i]), False, s.data_ptr(), s.numel(), P, n, n,
+                                source=view))
     return Trace(reqs, keep)
+
+
+def check_budget(trace: Trace, budget_bytes: int):
+    """A request whose output space exceeds the whole budget could never be
+    admitted: refuse the trace up front instead of waiting forever."""
+    for r in trace.requests:
+        if Arena._round(r.n_out_max) > budget_bytes:
+            raise ValueError(f"request {r.rid} needs {r.n_out_max} output bytes, "
+                             f"more than the {budget_bytes}-byte budget")
 
 
 def _stats(trace: Trace, extra: dict) -> dict:
@@ -130,12 +143,14 @@ def run_batched(torch, codec, trace: Trace, budget_bytes: int = 40 << 30, n_stre
                 max_group: int = 1024, on_done=None) -> dict:
     """Continuous batching.  on_done(request, out_tensor_view, size) is called
     for every request once its group has finished, before its space is freed."""
+    check_budget(trace, budget_bytes)
     arena_t = torch.empty(budget_bytes, dtype=torch.uint8, device="cuda")
     arena = Arena(budget_bytes)
     sizes_t = torch.zeros(len(trace.requests), dtype=torch.int64, device="cuda")
     base, nb = arena_t.data_ptr(), sizes_t.data_ptr()
     streams = [torch.cuda.Stream() for _ in range(n_streams)]
     busy = [None] * n_streams  # (event, group) per stream
+    plans = [[None, None] for _ in range(n_streams)]  # compress, decompress batch per stream
     origin = torch.cuda.Event(enable_timing=True)
     pending = trace.requests
     queue, groups = [], []
@@ -175,9 +190,14 @@ def run_batched(torch, codec, trace: Trace, budget_bytes: int = 40 << 30, n_stre
                     its = [(r.d_in, r.n_in, base + r.out_off, r.n_out_max, nb + 8 * r.rid,
                             r.params) for r in group if r.compress != d]
                     if its:
-                        b = lz.lz_batch_create(codec.ctx, its, decompress=d, stream=s.cuda_stream)
+                        b = plans[free[0]][d]
+                        if b is None:
+                            b = lz.lz_batch_create(codec.ctx, its, decompress=d,
+                                                   stream=s.cuda_stream)
+                            plans[free[0]][d] = b
+                        else:
+                            lz.lz_batch_update(codec.ctx, b, its, s.cuda_stream)
                         lz.lz_batch_run(codec.ctx, b, s.cuda_stream)
-                        lz.lz_batch_destroy(b, s.cuda_stream)  # freed after the run
                 ev = torch.cuda.Event(enable_timing=True)
                 ev.record(s)
                 busy[free[0]] = (ev, group)
@@ -187,6 +207,11 @@ def run_batched(torch, codec, trace: Trace, budget_bytes: int = 40 << 30, n_stre
             wait = pending[nxt].arrival - (time.perf_counter() - t0)
             if wait > 0.0002:
                 time.sleep(min(wait, 0.0005))
+    torch.cuda.synchronize()
+    for pair, s in zip(plans, streams):
+        for b in pair:
+            if b is not None:
+                lz.lz_batch_destroy(b, s.cuda_stream)
     torch.cuda.synchronize()
     st = codec.sync()
     if st != lz.LZ_OK:
@@ -199,6 +224,7 @@ def run_batched(torch, codec, trace: Trace, budget_bytes: int = 40 << 30, n_stre
 def run_plain(torch, codec, trace: Trace, budget_bytes: int = 40 << 30, on_done=None) -> dict:
     """One plain launch per request, in arrival order, on one stream; output
     space from the same kind of budgeted arena."""
+    check_budget(trace, budget_bytes)
     arena_t = torch.empty(budget_bytes, dtype=torch.uint8, device="cuda")
     arena = Arena(budget_bytes)
     sizes_t = torch.zeros(len(trace.requests), dtype=torch.int64, device="cuda")

@@ -68,6 +68,8 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.lz_sync(None, None) == lz.LZ_ERR_INVALID_ARG
     assert lib.lz_create(None, 0) == lz.LZ_ERR_INVALID_ARG
     assert lib.lz_compressed_bound(100, None) == 0
+    assert lib.lz_set_test_hooks(None, None) == lz.LZ_ERR_INVALID_ARG
+    assert lib.lz_batch_update(None, None, None, 0, None) == lz.LZ_ERR_INVALID_ARG
 
 
 def test_product_does_not_import_oracle():

@@ -1,6 +1,8 @@
 """The benchmark's reference arm on the host: the JSON line keeps the
 contract (impl, metric, unit, steps, warm-up, cpu_baseline, e2e with zero
-copies) and its value is the oracle's own throughput over the timed steps."""
+copies), carries the GPU arm's unit and dtype strings (so that the two
+lines can be divided), and its value is the oracle's own throughput on all
+host cores over the timed steps."""
 from __future__ import annotations
 
 import json
@@ -20,10 +22,13 @@ def test_reference_arm_line():
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference"
     assert line["steps"] == 2 and line["warmup"] == 1 and line["n_gpus"] == 1
-    assert line["unit"] == "GB/s" and line["higher_is_better"] is True
+    assert line["unit"] == "GB/s (input bytes compressed per second)"
+    assert line["higher_is_better"] is True
+    assert line["dtype"] == "u8/u32 symbols (integer/byte path, lossless)"
     assert line["value"] > 0 and line["ms_per_step"] > 0
     cb = line["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    assert cb["kind"] == "oracle" and cb["cores"] == (os.cpu_count() or 1)
+    assert cb["value"] == line["value"] and cb["unit"] == line["unit"] and cb["cpu_model"]
     assert "uint16 quant codes" in cb["sample"] and "2 timed steps" in cb["sample"]
     e2e = line["e2e"]
     assert e2e["value"] == line["value"]

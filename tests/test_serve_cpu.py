@@ -39,3 +39,15 @@ def test_arena_random_never_overlaps():
         for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
             assert a1 <= b0
         assert all(0 <= s0 and s1 <= 1 << 20 for s0, s1 in spans)
+
+
+def test_request_larger_than_budget_is_refused():
+    import pytest
+
+    from paper_2304_07342_gb300.serve import Request, Trace, check_budget
+    ok = Request(0, 0.0, True, 0, 1000, None, 1000, 1000)
+    big = Request(1, 0.001, True, 0, 5000, None, 4097, 4097)
+    check_budget(Trace([ok]), 4096)  # fits
+    with pytest.raises(ValueError):
+        check_budget(Trace([ok, big]), 4096)  # 4097 rounds to 4352 > 4096
+    check_budget(Trace([ok, big]), 4352)
