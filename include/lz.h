@@ -165,6 +165,30 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
                          const lz_params *p, const lz_options *opt, void *d_out,
                          uint64_t out_cap, uint64_t *d_out_bytes, lz_stream_t stream);
 
+/* Compression from host memory to host memory: the same stream as
+ * lz_compress of the same bytes, for callers whose data lives on the host.
+ * h_in (n_bytes) and h_out (capacity out_cap) are host buffers -- pinned
+ * (cudaHostAlloc / cudaHostRegister) for full speed; pageable memory works
+ * but its copies do not overlap.  The input is compressed in pieces of
+ * whole index superblocks (64 chunks, about 16 MiB a piece): chunks are
+ * independent (section 3.3.1), so each piece's records are exactly the
+ * whole input's.  Copying a piece in, compressing it and copying its table
+ * entries and records out to their final places in h_out run on three
+ * streams of the context and overlap with the neighbouring pieces; the
+ * host waits for a piece's stream size before placing its records and
+ * writes the header and the (rebased) index entries itself.  The call is
+ * synchronous: it starts after the work already enqueued on `stream` and
+ * returns when h_out holds the stream, its size in *h_out_bytes (host).
+ * Device errors of this call are returned by it (and cleared), not left
+ * for lz_sync.  LZ_ERR_BUFFER_TOO_SMALL when out_cap is below the stream
+ * size (then *h_out_bytes is the size needed and h_out is incomplete);
+ * LZ_ERR_NOMEM when the context cannot hold its device slots (3 pieces and
+ * their streams) or pinned staging; argument errors as for lz_compress
+ * (stream version 1, exact matcher). */
+lz_status lz_compress_host(lz_ctx *ctx, const void *h_in, uint64_t n_bytes, const lz_params *p,
+                           void *h_out, uint64_t out_cap, uint64_t *h_out_bytes,
+                           lz_stream_t stream);
+
 /* Read and validate the header of the stream at d_in (in_bytes long) and
  * return its decompressed size in *h_n.  Synchronises `stream` (it copies
  * the 32-byte header to the host).  LZ_ERR_CORRUPT for a bad header. */

@@ -15,11 +15,12 @@
 //     token): the flag word gives each token's payload offset by popcount,
 //     a shuffle scan of token lengths gives its output position; a literal
 //     writes its symbol there, a pointer writes (offset - 1) into the slot
-//     of its first symbol, and both set their bit in a token-start bitmap
-//     (pointers also in a pointer-start bitmap).  Phase 2 takes the output
+//     of its first symbol, and both mark their first position (one byte
+//     per position: literal or pointer start).  Phase 2 takes the output
 //     positions 32 at a time (lane = position): the owning token is the
-//     last set start bit at or before the position (one bit scan; a token
-//     that began in an earlier round is carried in registers), a position
+//     last marked position at or before the position (a ballot and a bit
+//     scan; a token that began in an earlier round is carried in
+//     registers), a position
 //     inside a pointer copies from position - offset, and sources inside
 //     the same 32 positions are resolved by pointer jumping over the lanes;
 //     earlier positions are final, later rounds read them;
@@ -187,7 +188,7 @@ __device__ __forceinline__ void copy_s2g(uint8_t *dst, const uint8_t *src,
 // A warp's shared-memory slice (see DecodeLayout).
 struct Slice {
   uint64_t *bar;
-  uint32_t *sbits, *mbits;  // token starts, pointer starts (one bit per position)
+  uint8_t *marks;           // per position: 0 inside a token, 1 literal start, 2 pointer start
   uint8_t *hi;              // high bytes of (offset - 1), or nullptr
   uint8_t *outb;            // output image, or nullptr (decode into the output)
   uint8_t *win;             // record window, or nullptr (read the record in place)
@@ -197,8 +198,7 @@ struct Slice {
 __device__ __forceinline__ Slice make_slice(uint8_t *ws, const DecodeLayout &L, bool hi) {
   Slice sl;
   sl.bar = reinterpret_cast<uint64_t *>(ws);
-  sl.sbits = reinterpret_cast<uint32_t *>(ws + L.bits_off);
-  sl.mbits = sl.sbits + L.bit_words;
+  sl.marks = ws + L.marks_off;
   sl.hi = hi ? ws + L.hi_off : nullptr;
   sl.outb = L.staged ? ws + L.out_off : nullptr;
   sl.win = L.staged ? ws + L.win_off : nullptr;
@@ -239,11 +239,11 @@ __device__ __forceinline__ bool decode_tokens(const Header &h, const uint8_t *fl
   const uint32_t offmask = h.offB == 2 ? 0xFFFFu : 0xFFu;
   const uint32_t lt = lanemask_lt(lane);
   const uint32_t fb = (ntok + 7) / 8;
-  const uint32_t nw = (k + 31) / 32;
-  uint32_t *sbits = sl.sbits, *mbits = sl.mbits;
-  for (uint32_t i = lane; i < nw; i += 32) {
-    sbits[i] = 0;
-    mbits[i] = 0;
+  uint8_t *marks = sl.marks;
+  {
+    uint4 *m16 = reinterpret_cast<uint4 *>(marks);
+    const uint32_t n16 = ((k + 31) & ~31u) / 16;
+    for (uint32_t i = lane; i < n16; i += 32) m16[i] = make_uint4(0, 0, 0, 0);
   }
   __syncwarp();
 
@@ -260,9 +260,7 @@ __device__ __forceinline__ bool decode_tokens(const Header &h, const uint8_t *fl
   np = __reduce_add_sync(kFull, np);
   if (S * (ntok - np) + tsz * np != pay_tok) return false;
   auto put = [&](uint32_t st, bool m, uint32_t off, uint32_t w) {
-    const uint32_t bit = 1u << (st & 31u);
-    atomicOr(&sbits[st >> 5], bit);
-    if (m) atomicOr(&mbits[st >> 5], bit);
+    marks[st] = m ? 2 : 1;
     st_slot<S>(ob, st, m ? off - 1u : w, aligned);
     if (S == 1 && sl.hi && m) sl.hi[st] = static_cast<uint8_t>((off - 1u) >> 8);
   };
@@ -333,7 +331,8 @@ __device__ __forceinline__ bool decode_tokens(const Header &h, const uint8_t *fl
   for (uint32_t r0 = 0; r0 < k; r0 += 32) {
     const uint32_t j = r0 + lane;
     const bool act = j < k;
-    const uint32_t sw = sbits[r0 >> 5], mw = mbits[r0 >> 5];
+    const uint32_t mk = marks[j];  // zero past k
+    const uint32_t sw = __ballot_sync(kFull, mk != 0), mw = __ballot_sync(kFull, mk == 2);
     uint32_t raw = act ? ld_slot<S>(ob, j, aligned) : 0u;
     if (S == 1 && sl.hi && act) raw |= static_cast<uint32_t>(sl.hi[j]) << 8;
     const uint32_t mb = sw & le;
@@ -564,7 +563,7 @@ __global__ void __launch_bounds__(1024, 1) decompress_batch_kernel(const Decompr
     // the header must still be the one the plan sized the slices for
     const uint64_t kh = ok ? h.C / h.S : 0;
     const bool need_hi = ok && h.S == 1 && h.offB == 2;
-    const bool fits = ok && h.nc == it.nc && (kh + 31) / 32 <= B.lay.bit_words &&
+    const bool fits = ok && h.nc == it.nc && kh <= B.lay.mark_bytes &&
                       (!need_hi || B.lay.out_off - B.lay.hi_off >= kh) &&
                       (!B.lay.staged ||
                        (h.C + 16 <= B.lay.win_off - B.lay.out_off &&

@@ -113,14 +113,15 @@ struct DecItem {
 };
 
 // Per-warp shared-memory slice of the decoder (byte offsets, 16-byte
-// aligned): an mbarrier, two bitmaps over the chunk's positions (token
-// starts and pointer starts), the high bytes of (offset - 1) when one-byte
-// symbols carry two-byte offsets, then -- when they fit -- the chunk's output
-// and a window for its record.  Without them (`staged` false) a warp
-// decodes straight into the output buffer and reads the record in place.
+// aligned): an mbarrier, one mark byte per position of the chunk (0 inside
+// a token, 1 where a literal starts, 2 where a pointer starts), the high
+// bytes of (offset - 1) when one-byte symbols carry two-byte offsets, then
+// -- when they fit -- the chunk's output and a window for its record.
+// Without them (`staged` false) a warp decodes straight into the output
+// buffer and reads the record in place.
 struct DecodeLayout {
-  uint32_t bits_off;   // token-start bitmap; the pointer-start bitmap follows
-  uint32_t bit_words;  // 32-bit words per bitmap
+  uint32_t marks_off;  // mark bytes, a multiple of 32
+  uint32_t mark_bytes;
   uint32_t hi_off;     // k bytes (one-byte symbols, two-byte offsets) or none
   uint32_t out_off;    // C bytes + 16 slack
   uint32_t win_off;    // largest record + 64 slack
@@ -143,10 +144,9 @@ __host__ __device__ inline DecodeLayout decode_layout(uint64_t kmax, uint64_t cm
                                                       uint64_t rmax, bool hi, uint64_t budget) {
   DecodeLayout L{};
   uint64_t at = 16;  // mbarrier
-  L.bits_off = static_cast<uint32_t>(at);
-  L.bit_words = static_cast<uint32_t>((kmax + 31) / 32);
-  at += 8ull * L.bit_words;
-  at = (at + 15) & ~15ull;
+  L.marks_off = static_cast<uint32_t>(at);
+  L.mark_bytes = static_cast<uint32_t>((kmax + 31) & ~31ull);
+  at += L.mark_bytes;
   L.hi_off = static_cast<uint32_t>(at);
   if (hi) at += (kmax + 15) & ~15ull;
   const uint64_t base = at;

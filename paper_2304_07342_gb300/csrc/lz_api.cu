@@ -81,6 +81,13 @@ struct lz_ctx {
   uint32_t *d_err = nullptr;
   std::mutex mu;
   lz_test_hooks hooks{};    // test hooks (lz_set_test_hooks); all zero normally
+  // lz_compress_host: copy/compute streams, device slots, pinned staging
+  cudaStream_t hs[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t hev[10] = {};
+  void *hdev = nullptr;       // device slots (input piece, piece stream, size)
+  size_t hdev_bytes = 0;
+  void *hpin = nullptr;       // pinned: per slot a size and the piece's index entries
+  size_t hpin_bytes = 0;
 };
 
 namespace {
@@ -179,6 +186,10 @@ lz_status reserve_scratch(lz_ctx *ctx, size_t bytes) {
   return LZ_OK;
 }
 
+lz_status compress_locked(lz_ctx *ctx, const void *d_in, uint64_t n_bytes, const lz_params *p,
+                          uint32_t match, uint32_t version, void *d_out, uint64_t out_cap,
+                          unsigned long long *out_bytes, cudaStream_t st);
+
 }  // namespace
 
 extern "C" {
@@ -263,6 +274,12 @@ void lz_destroy(lz_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  for (cudaStream_t &h : ctx->hs)
+    if (h) cudaStreamDestroy(h);
+  for (cudaEvent_t &e : ctx->hev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->hdev) cudaFree(ctx->hdev);
+  if (ctx->hpin) cudaFreeHost(ctx->hpin);
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->d_err) cudaFree(ctx->d_err);
   delete ctx;
@@ -296,8 +313,24 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lock(ctx->mu);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
+  return compress_locked(ctx, d_in, n_bytes, p, match, version, d_out, out_cap,
+                         reinterpret_cast<unsigned long long *>(d_out_bytes), st);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Enqueue one compression whose arguments lz_compress_ex has checked, with
+// the context's lock held and its device current.
+lz_status compress_locked(lz_ctx *ctx, const void *d_in, uint64_t n_bytes, const lz_params *p,
+                          uint32_t match, uint32_t version, void *d_out, uint64_t out_cap,
+                          unsigned long long *out_bytes, cudaStream_t st) {
+  const uint32_t S = p->symbol_bytes, C = p->chunk_bytes;
+  const uint64_t nc = div_up(n_bytes, C);
+  const uint64_t records_at = glz::kHeaderBytes + glz::kTableEntry * nc +
+                              8ull * div_up(nc, glz::kIndexStride);
   const uint32_t offB = off_bytes(p->window);
-  auto *out_bytes = reinterpret_cast<unsigned long long *>(d_out_bytes);
   if (nc == 0)
     return cuda_status(glz::launch_header(static_cast<uint8_t *>(d_out), version, S, offB,
                                           p->min_match, p->max_match, C,
@@ -373,6 +406,176 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
     default: e = glz::launch_compress_s4(A, nj, block, g, st); break;
   }
   return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+lz_status lz_compress_host(lz_ctx *ctx, const void *h_in, uint64_t n_bytes, const lz_params *p,
+                           void *h_out, uint64_t out_cap, uint64_t *h_out_bytes,
+                           lz_stream_t stream) {
+  if (!ctx || !params_ok(p) || !h_out || !h_out_bytes || (n_bytes > 0 && !h_in))
+    return LZ_ERR_INVALID_ARG;
+  const uint32_t S = p->symbol_bytes, C = p->chunk_bytes;
+  if (n_bytes % S != 0) return LZ_ERR_INVALID_ARG;
+  const uint64_t nc = div_up(n_bytes, C);
+  if (nc > kMaxLaunchChunks) return LZ_ERR_INVALID_ARG;
+  const uint64_t records_at = glz::kHeaderBytes + glz::kTableEntry * nc +
+                              8ull * div_up(nc, glz::kIndexStride);
+  if (out_cap < records_at) return LZ_ERR_BUFFER_TOO_SMALL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
+  uint8_t *out = static_cast<uint8_t *>(h_out);
+  const uint8_t *in = static_cast<const uint8_t *>(h_in);
+  // the header, written on the host
+  {
+    uint8_t h[glz::kHeaderBytes] = {'G', 'L', 'Z', '1', 1, static_cast<uint8_t>(S),
+                                    static_cast<uint8_t>(off_bytes(p->window)),
+                                    static_cast<uint8_t>(p->min_match),
+                                    static_cast<uint8_t>(p->max_match)};
+    for (int i = 0; i < 4; ++i) {
+      h[12 + i] = static_cast<uint8_t>(C >> (8 * i));
+      h[16 + i] = static_cast<uint8_t>(p->window >> (8 * i));
+      h[20 + i] = static_cast<uint8_t>(nc >> (8 * i));
+    }
+    for (int i = 0; i < 8; ++i) h[24 + i] = static_cast<uint8_t>(n_bytes >> (8 * i));
+    std::memcpy(out, h, sizeof(h));
+  }
+  if (nc == 0) {
+    *h_out_bytes = records_at;
+    return LZ_OK;
+  }
+  // pieces of whole index superblocks, about 16 MiB, in three rotating slots
+  constexpr int kSlots = 3;
+  const uint64_t sb = glz::kIndexStride * static_cast<uint64_t>(C);
+  const uint64_t piece = std::max<uint64_t>(sb, ((16ull << 20) / sb) * sb);
+  const uint64_t npieces = div_up(n_bytes, piece);
+  const uint64_t piece_cap = (lz_compressed_bound(piece, p) + 255) & ~255ull;
+  const uint64_t slot_dev = ((piece + 255) & ~255ull) + piece_cap + 256;
+  const uint64_t piece_idx = div_up(piece / C, glz::kIndexStride);
+  const uint64_t slot_pin = 8 + 8 * piece_idx;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+    if (!ctx->hs[i]) e = cudaStreamCreateWithFlags(&ctx->hs[i], cudaStreamNonBlocking);
+  for (int i = 0; i < 10 && e == cudaSuccess; ++i)
+    if (!ctx->hev[i]) e = cudaEventCreateWithFlags(&ctx->hev[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (ctx->hdev_bytes < kSlots * slot_dev) {
+    if (ctx->hooks.fail_alloc) return LZ_ERR_NOMEM;
+    if (ctx->hdev) cudaFree(ctx->hdev);
+    ctx->hdev = nullptr;
+    ctx->hdev_bytes = 0;
+    if ((e = cudaMalloc(&ctx->hdev, kSlots * slot_dev)) != cudaSuccess) return cuda_status(e);
+    ctx->hdev_bytes = kSlots * slot_dev;
+  }
+  if (ctx->hpin_bytes < kSlots * slot_pin) {
+    if (ctx->hooks.fail_alloc) return LZ_ERR_NOMEM;
+    if (ctx->hpin) cudaFreeHost(ctx->hpin);
+    ctx->hpin = nullptr;
+    ctx->hpin_bytes = 0;
+    if ((e = cudaMallocHost(&ctx->hpin, kSlots * slot_pin)) != cudaSuccess)
+      return cuda_status(e);
+    ctx->hpin_bytes = kSlots * slot_pin;
+  }
+  cudaStream_t s_in = ctx->hs[0], s_comp = ctx->hs[1], s_out = ctx->hs[2];
+  cudaEvent_t *ev_in = ctx->hev, *ev_comp = ctx->hev + 3, *ev_out = ctx->hev + 6;
+  cudaEvent_t ev_start = ctx->hev[9];
+  uint8_t *dev = static_cast<uint8_t *>(ctx->hdev);
+  uint8_t *pin = static_cast<uint8_t *>(ctx->hpin);
+  auto slot_in = [&](int sl) { return dev + sl * slot_dev; };
+  auto slot_stream = [&](int sl) { return slot_in(sl) + ((piece + 255) & ~255ull); };
+  auto slot_size = [&](int sl) {
+    return reinterpret_cast<unsigned long long *>(slot_stream(sl) + piece_cap);
+  };
+  auto pin_size = [&](int sl) { return reinterpret_cast<uint64_t *>(pin + sl * slot_pin); };
+  auto pin_idx = [&](int sl) { return pin_size(sl) + 1; };
+  if (cudaEventRecord(ev_start, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess ||
+      cudaStreamWaitEvent(s_in, ev_start, 0) != cudaSuccess)
+    return LZ_ERR_CUDA;
+  lz_status st = LZ_OK;
+  // copy-in and compression of piece i (slot i % 3; the slot's previous
+  // piece has been copied out once ev_out fires)
+  auto issue = [&](uint64_t i) -> lz_status {
+    const int sl = static_cast<int>(i % kSlots);
+    const uint64_t at = i * piece, len = std::min(piece, n_bytes - at);
+    if (i >= kSlots && cudaStreamWaitEvent(s_in, ev_out[sl], 0) != cudaSuccess) return LZ_ERR_CUDA;
+    if (cudaMemcpyAsync(slot_in(sl), in + at, len, cudaMemcpyHostToDevice, s_in) != cudaSuccess ||
+        cudaEventRecord(ev_in[sl], s_in) != cudaSuccess ||
+        cudaStreamWaitEvent(s_comp, ev_in[sl], 0) != cudaSuccess)
+      return LZ_ERR_CUDA;
+    lz_status r = compress_locked(ctx, slot_in(sl), len, p, LZ_MATCH_EXACT, 1, slot_stream(sl),
+                                  piece_cap, slot_size(sl), s_comp);
+    if (r != LZ_OK) return r;
+    const uint64_t pc = div_up(len, C), pidx = div_up(pc, glz::kIndexStride);
+    if (cudaMemcpyAsync(pin_size(sl), slot_size(sl), 8, cudaMemcpyDeviceToHost, s_comp) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(pin_idx(sl), slot_stream(sl) + glz::kHeaderBytes + 8 * pc, 8 * pidx,
+                        cudaMemcpyDeviceToHost, s_comp) != cudaSuccess ||
+        cudaEventRecord(ev_comp[sl], s_comp) != cudaSuccess)
+      return LZ_ERR_CUDA;
+    return LZ_OK;
+  };
+  uint64_t rec_base = 0;  // record bytes of the pieces before
+  bool fits = true;
+  for (uint64_t i = 0; i < std::min<uint64_t>(kSlots, npieces) && st == LZ_OK; ++i) st = issue(i);
+  for (uint64_t i = 0; i < npieces && st == LZ_OK; ++i) {
+    const int sl = static_cast<int>(i % kSlots);
+    const uint64_t at = i * piece, len = std::min(piece, n_bytes - at);
+    const uint64_t pc = div_up(len, C), pidx = div_up(pc, glz::kIndexStride);
+    const uint64_t cb = at / C;  // chunks before the piece (a multiple of 64)
+    const uint64_t p_records_at = glz::kHeaderBytes + 8 * pc + 8 * pidx;
+    if (cudaEventSynchronize(ev_comp[sl]) != cudaSuccess) {
+      st = LZ_ERR_CUDA;
+      break;
+    }
+    const uint64_t size = *pin_size(sl);
+    const uint64_t rec = size >= p_records_at ? size - p_records_at : 0;
+    fits = fits && records_at + rec_base + rec <= out_cap;
+    if (fits) {
+      for (uint64_t j = 0; j < pidx; ++j) {  // index entries, rebased
+        const uint64_t v = pin_idx(sl)[j] + rec_base;
+        uint8_t *d = out + glz::kHeaderBytes + 8 * nc + 8 * (cb / glz::kIndexStride + j);
+        for (int b = 0; b < 8; ++b) d[b] = static_cast<uint8_t>(v >> (8 * b));
+      }
+      if (cudaStreamWaitEvent(s_out, ev_comp[sl], 0) != cudaSuccess ||
+          cudaMemcpyAsync(out + glz::kHeaderBytes + 8 * cb, slot_stream(sl) + glz::kHeaderBytes,
+                          8 * pc, cudaMemcpyDeviceToHost, s_out) != cudaSuccess ||
+          cudaMemcpyAsync(out + records_at + rec_base, slot_stream(sl) + p_records_at, rec,
+                          cudaMemcpyDeviceToHost, s_out) != cudaSuccess) {
+        st = LZ_ERR_CUDA;
+        break;
+      }
+    } else if (cudaStreamWaitEvent(s_out, ev_comp[sl], 0) != cudaSuccess) {
+      st = LZ_ERR_CUDA;
+      break;
+    }
+    if (cudaEventRecord(ev_out[sl], s_out) != cudaSuccess) {
+      st = LZ_ERR_CUDA;
+      break;
+    }
+    rec_base += rec;
+    if (i + kSlots < npieces) st = issue(i + kSlots);
+  }
+  // finish the copies (also after an error: the slots must be idle)
+  cudaStreamSynchronize(s_in);
+  cudaStreamSynchronize(s_comp);
+  if (cudaStreamSynchronize(s_out) != cudaSuccess && st == LZ_OK) st = LZ_ERR_CUDA;
+  // device-side errors of the compressions, returned here (and cleared)
+  uint32_t h = 0;
+  if (cudaMemcpy(&h, ctx->d_err, 4, cudaMemcpyDeviceToHost) != cudaSuccess && st == LZ_OK)
+    st = LZ_ERR_CUDA;
+  if (h) {
+    cudaMemset(ctx->d_err, 0, 4);
+    if (st == LZ_OK)
+      st = (h & glz::kErrInternal)  ? LZ_ERR_INTERNAL
+           : (h & glz::kErrTimeout) ? LZ_ERR_TIMEOUT
+           : (h & glz::kErrCorrupt) ? LZ_ERR_CORRUPT
+                                    : LZ_ERR_BUFFER_TOO_SMALL;
+  }
+  if (st != LZ_OK) return st;
+  *h_out_bytes = records_at + rec_base;
+  return fits ? LZ_OK : LZ_ERR_BUFFER_TOO_SMALL;
 }
 
 lz_status lz_decompressed_size(const void *d_in, uint64_t in_bytes,

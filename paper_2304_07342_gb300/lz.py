@@ -34,7 +34,7 @@ _NAMES = {0: "LZ_OK", 1: "LZ_ERR_INVALID_ARG", 2: "LZ_ERR_BUFFER_TOO_SMALL",
 
 # every symbol include/lz.h declares
 EXPORTS = ("lz_create", "lz_destroy", "lz_status_string", "lz_check_params",
-           "lz_compressed_bound", "lz_compress", "lz_compress_ex", "lz_decompressed_size",
+           "lz_compressed_bound", "lz_compress", "lz_compress_ex", "lz_compress_host", "lz_decompressed_size",
            "lz_decompress", "lz_sync", "lz_compress_noalloc", "lz_batch_create",
            "lz_batch_run", "lz_batch_update", "lz_batch_destroy", "lz_autotune", "lz_stitch", "lz_batch_create_ex",
            "lz_select_params", "lz_huff_bound", "lz_huff_compress",
@@ -109,6 +109,8 @@ def load(path: str = LIB_PATH):
     lib.lz_compress.restype = i32
     lib.lz_compress_ex.argtypes = [vp, vp, u64, pp, ctypes.POINTER(lz_options), vp, u64, vp, vp]
     lib.lz_compress_ex.restype = i32
+    lib.lz_compress_host.argtypes = [vp, vp, u64, pp, vp, u64, ctypes.POINTER(u64), vp]
+    lib.lz_compress_host.restype = i32
     lib.lz_decompressed_size.argtypes = [vp, u64, ctypes.POINTER(u64), vp]
     lib.lz_decompressed_size.restype = i32
     lib.lz_decompress.argtypes = [vp, vp, u64, vp, u64, vp, vp]
@@ -190,6 +192,15 @@ def lz_compress_ex(ctx: int, d_in: int, n_bytes: int, p: Params, d_out: int, out
     opt = lz_options(match, version)
     _check(load().lz_compress_ex(ctx, d_in, n_bytes, ctypes.byref(p.c()), ctypes.byref(opt),
                                  d_out, out_cap, d_out_bytes, stream), "lz_compress_ex")
+
+
+def lz_compress_host(ctx: int, h_in: int, n_bytes: int, p: Params, h_out: int, out_cap: int,
+                     stream: int = 0) -> int:
+    """Host buffer in, host buffer out (synchronous); returns the stream size."""
+    nb = ctypes.c_uint64()
+    _check(load().lz_compress_host(ctx, h_in, n_bytes, ctypes.byref(p.c()), h_out, out_cap,
+                                   ctypes.byref(nb), stream), "lz_compress_host")
+    return nb.value
 
 
 def lz_decompressed_size(d_in: int, in_bytes: int, stream: int = 0) -> int:
