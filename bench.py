@@ -579,11 +579,13 @@ def _batched(torch, codec, args, n_buffers: int = 10_000):
     plain launch per buffer (compress and decompress of every buffer)."""
     from paper_2304_07342_gb300 import batch
     t = time.perf_counter()
-    w = batch.build(torch, n_buffers=n_buffers, seed=args.seed, autotune_codec=codec)
+    tuning = []
+    w = batch.build(torch, n_buffers=n_buffers, seed=args.seed, autotune_codec=codec,
+                    report=tuning)
     build_s = time.perf_counter() - t
     r = batch.run(torch, codec, w, steps=3)
     r.update({"workload": f"{n_buffers} buffers, log-uniform 4 KiB-16 MiB, 4 kinds",
-              "setup_seconds": round(build_s, 2),
+              "setup_seconds": round(build_s, 2), "autotune": tuning,
               "speedup_vs_per_buffer": round(r["compress_batched_gbs"] /
                                              r["compress_per_buffer_gbs"], 3)})
     del w

@@ -146,6 +146,11 @@ typedef struct lz_options {
                        chunk's 1..S-1 bytes after its last whole symbol
                        follow its tokens as they are, counted in its
                        payload_bytes.  lz_decompress reads both.       */
+  uint32_t warps_per_block; /* compression launch shape: warps per block
+                       (one chunk per warp at a time): 1, 2, 4 or 8;
+                       0 = the library's choice, the one that keeps the
+                       most warps resident.  It changes how chunks are
+                       spread over the GPU, never the stream.          */
 } lz_options;
 
 /* lz_compress with options (opt may be NULL: the defaults).
@@ -167,24 +172,26 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
 
 /* Compression from host memory to host memory: the same stream as
  * lz_compress of the same bytes, for callers whose data lives on the host.
- * h_in (n_bytes) and h_out (capacity out_cap) are host buffers -- pinned
- * (cudaHostAlloc / cudaHostRegister) for full speed; pageable memory works
- * but its copies do not overlap.  The input is compressed in pieces of
- * whole index superblocks (64 chunks, about 16 MiB a piece): chunks are
- * independent (section 3.3.1), so each piece's records are exactly the
- * whole input's.  Copying a piece in, compressing it and copying its table
- * entries and records out to their final places in h_out run on three
- * streams of the context and overlap with the neighbouring pieces; the
- * host waits for a piece's stream size before placing its records and
- * writes the header and the (rebased) index entries itself.  The call is
+ * h_in (n_bytes) and h_out (capacity out_cap) are host buffers.  The input
+ * is copied to the device in pieces of whole index superblocks (64 chunks,
+ * about 16 MiB a piece), and each piece is compressed by a launch over its
+ * own chunks as soon as it has arrived, while the next piece is copied:
+ * chunks are independent (section 3.3.1) and the look-back of a piece's
+ * first chunks reaches into the pieces before it, which are complete.
+ * When h_out is pinned (cudaHostAlloc / cudaHostRegister, mapped into the
+ * device's address space; on GB300 the NVLink-C2C link carries the
+ * writes), the kernels write header, table, index and records straight to
+ * their final places in it; otherwise the stream goes through a device
+ * buffer and is copied out at the end.  Pinned h_in lets the copies overlap
+ * the compression.  The context holds device memory for the input (and for
+ * the stream when h_out is not pinned) between calls.  The call is
  * synchronous: it starts after the work already enqueued on `stream` and
- * returns when h_out holds the stream, its size in *h_out_bytes (host).
- * Device errors of this call are returned by it (and cleared), not left
- * for lz_sync.  LZ_ERR_BUFFER_TOO_SMALL when out_cap is below the stream
- * size (then *h_out_bytes is the size needed and h_out is incomplete);
- * LZ_ERR_NOMEM when the context cannot hold its device slots (3 pieces and
- * their streams) or pinned staging; argument errors as for lz_compress
- * (stream version 1, exact matcher). */
+ * returns when h_out holds the stream and *h_out_bytes (host) its size.
+ * Device errors of this call are returned by it (and cleared), not left for
+ * lz_sync.  LZ_ERR_BUFFER_TOO_SMALL when out_cap is below the stream size
+ * (then *h_out_bytes is the size needed and h_out is incomplete);
+ * LZ_ERR_NOMEM when the device memory cannot be had; argument errors as
+ * for lz_compress (stream version 1, exact matcher). */
 lz_status lz_compress_host(lz_ctx *ctx, const void *h_in, uint64_t n_bytes, const lz_params *p,
                            void *h_out, uint64_t out_cap, uint64_t *h_out_bytes,
                            lz_stream_t stream);
@@ -305,16 +312,37 @@ void lz_batch_destroy(lz_batch *batch, lz_stream_t stream);
 
 /* Choose chunk_bytes and window for data of `symbol_bytes`-byte symbols from
  * timed trial compressions of a device-resident sample: among C in {2048,
- * 4096, 8192} and W in {64, 128, 256} whose compression ratio is within 2%
- * of the best ratio found, the smallest C that is within 10% of the fastest
- * time (less shared memory per warp, which helps a batched launch over
- * buffers of several kinds), then the fastest; min_match 3 (2 for 4-byte symbols),
- * max_match 255.  The choice changes the stream (it is recorded in its
- * header), never the arithmetic: the stream is exactly what lz_compress
- * produces with the chosen parameters.  Synchronous; allocates and frees
- * temporary device buffers. */
+ * 4096, 8192, 16384} and W in {64, 128, 256, 512} whose compression ratio
+ * is within 2% of the best ratio found, the smallest C that is within 10%
+ * of the fastest time (less shared memory per warp, which helps a batched
+ * launch over buffers of several kinds), then the fastest; min_match 3 (2
+ * for 4-byte symbols), max_match 255.  The choice changes the stream (it is
+ * recorded in its header), never the arithmetic: the stream is exactly
+ * what lz_compress produces with the chosen parameters.  Synchronous;
+ * allocates and frees temporary device buffers. */
 lz_status lz_autotune(lz_ctx *ctx, const void *d_sample, uint64_t sample_bytes,
                       uint32_t symbol_bytes, lz_params *out);
+
+/* One trial of lz_autotune_ex: the parameters, the launch shape
+ * (lz_options.warps_per_block; 0 = the library's choice), the mean time of
+ * one compression of the sample in seconds, and the compression ratio. */
+typedef struct lz_tune_trial {
+  lz_params params;
+  uint32_t warps_per_block;
+  double seconds;
+  double ratio;
+} lz_tune_trial;
+
+/* lz_autotune, then the launch shape for the chosen parameters: warps per
+ * block 1, 2, 4 and 8 (those that fit) are timed beside the library's own
+ * choice, and the fastest is returned in *out_warps_per_block (0 when the
+ * library's choice is within 2% of it); pass it in lz_options.  Every
+ * trial (the 16 parameter sets, then the shapes) is written to trials[0 ..
+ * min(max_trials, *n_trials)) and their count to *n_trials; either may be
+ * NULL, as may out_warps_per_block. */
+lz_status lz_autotune_ex(lz_ctx *ctx, const void *d_sample, uint64_t sample_bytes,
+                         uint32_t symbol_bytes, lz_params *out, uint32_t *out_warps_per_block,
+                         lz_tune_trial *trials, uint32_t max_trials, uint32_t *n_trials);
 
 /* The paper's parameter selection (section 3.2.3), for data whose elements
  * are dtype_bytes wide (1, 2 or 4) at compression level `level` (1-4,

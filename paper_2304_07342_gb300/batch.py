@@ -51,20 +51,24 @@ def make_pools(torch, pool_bytes: int = 256 << 20, seed: int = 0, device="cuda")
             for a in arrs]
 
 
-def autotuned_params(codec, pools, sample_bytes: int = 8 << 20) -> list:
-    """Chunk size and window per kind from ``lz_autotune`` on the head of
-    each kind's pool.  One launch sizes every warp's shared memory for the
-    largest chunk of the batch, so a kind whose sample does not compress
-    (where a large chunk only saves per-chunk overhead) is held to the
-    largest chunk chosen for a kind that does compress."""
+def autotuned_params(codec, pools, sample_bytes: int = 8 << 20, report: list | None = None) -> list:
+    """Chunk size and window per kind from ``lz_autotune_ex`` on the head of
+    each kind's pool (its launch-shape choice and every trial go to
+    `report`).  One launch sizes every warp's shared memory for the largest
+    chunk of the batch, so a kind whose sample does not compress (where a
+    large chunk only saves per-chunk overhead) is held to the largest chunk
+    chosen for a kind that does compress."""
     out, ratios = [], []
     for k, pool in enumerate(pools):
         n = min(pool.numel(), sample_bytes)
         n -= n % KIND_S[k]
-        p = lz.lz_autotune(codec.ctx, pool.data_ptr(), n, KIND_S[k])
+        p, wpb, trials = lz.lz_autotune_ex(codec.ctx, pool.data_ptr(), n, KIND_S[k])
         s = codec.compress_sync(pool[:n], p)
         out.append(p)
         ratios.append(n / max(1, s.numel()))
+        if report is not None:
+            report.append({"kind": KIND_NAMES[k], "chosen": dict(S=p.S, C=p.C, W=p.W, m=p.m, M=p.M),
+                           "warps_per_block": wpb, "trials": trials})
     return hold_chunks(out, ratios)
 
 
@@ -83,7 +87,7 @@ def hold_chunks(params: list, ratios: list, min_ratio: float = 1.05) -> list:
 
 def build(torch, n_buffers: int = 10_000, seed: int = 0, params=None, pools=None,
           lo_bytes: int = 4096, hi_bytes: int = 16 << 20, device="cuda",
-          autotune_codec=None) -> Workload:
+          autotune_codec=None, report: list | None = None) -> Workload:
     """Buffers are 16-byte aligned slices of the pools; outputs live in one
     arena at 256-byte aligned offsets.  Parameters per kind: ``params``, else
     autotuned when a codec is given, else fixed defaults."""
@@ -91,7 +95,7 @@ def build(torch, n_buffers: int = 10_000, seed: int = 0, params=None, pools=None
                                        hi_bytes=hi_bytes)
     pools = pools if pools is not None else make_pools(torch, seed=seed, device=device)
     if params is None and autotune_codec is not None:
-        params = autotuned_params(autotune_codec, pools)
+        params = autotuned_params(autotune_codec, pools, report=report)
     if params is None:
         params = [lz.Params(KIND_S[k], 4096 if KIND_S[k] < 4 else 8192,
                             128 if KIND_S[k] < 4 else 256, 3 if KIND_S[k] < 4 else 2)
@@ -190,7 +194,14 @@ def run(torch, codec, w: Workload, steps: int = 3, check: int = 64) -> dict:
     db = lz.lz_batch_create(codec.ctx, ditems, decompress=True, stream=stream.cuda_stream)
     torch.cuda.synchronize()
     try:
-        t_dbatch = time_gpu(torch, lambda: lz.lz_batch_run(codec.ctx, db, stream.cuda_stream), steps)
+        # one run, then the run captured in a CUDA graph and replayed
+        with torch.cuda.stream(g_stream):
+            lz.lz_batch_run(codec.ctx, db, g_stream.cuda_stream)
+        torch.cuda.synchronize()
+        dgraph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(dgraph, stream=g_stream):
+            lz.lz_batch_run(codec.ctx, db, g_stream.cuda_stream)
+        t_dbatch = time_gpu(torch, dgraph.replay, steps)
 
         def per_buffer_dec():
             for it in ditems:
@@ -215,6 +226,7 @@ def run(torch, codec, w: Workload, steps: int = 3, check: int = 64) -> dict:
         "ratio": round(n / float(sizes.sum()), 4),
         "sizes_equal_per_buffer": bool(same),
         "launches": {"batched": 2, "per_buffer": 2 * len(items)},
+        "graphs": "both batched runs replayed from captured CUDA graphs",
         "params": [dict(kind=KIND_NAMES[k], S=p.S, C=p.C, W=p.W, m=p.m, M=p.M)
                    for k, p in enumerate(w.params)],
     })

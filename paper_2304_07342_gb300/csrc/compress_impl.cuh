@@ -160,21 +160,22 @@ __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
       const uint32_t p = base + lane;
       const bool ok = okk[u];
       const uint32_t h = hh[u];
-      const uint32_t old = ok ? table[h] : kNoPos;
+      const bool hok = GLZ_OK(h < H);
+      const uint32_t old = ok && hok ? table[h] : kNoPos;
       __syncwarp();
-      if (ok) table[h] = static_cast<uint16_t>(p);
+      if (ok && hok) table[h] = static_cast<uint16_t>(p);
       __syncwarp();
-      const bool lost = ok && table[h] != p;
+      const bool lost = ok && hok && table[h] != p;
       uint32_t q = old;
       if (__any_sync(kFull, lost)) {
         const uint32_t grp = __match_any_sync(kFull, ok ? h : (0x10000u + lane));
         const uint32_t lower = grp & lt;
         if (lower) q = base + (31u - __clz(lower));
         __syncwarp();
-        if (ok && (grp >> lane) == 1u) table[h] = static_cast<uint16_t>(p);  // last wins
+        if (ok && hok && (grp >> lane) == 1u) table[h] = static_cast<uint16_t>(p);  // last wins
       }
       const uint32_t dist = (ok && q != kNoPos && p - q <= A.W) ? p - q : 0u;
-      if (p < k) links.set(p, dist);
+      if (p < k && GLZ_OK(dist <= p)) links.set(p, dist);
       qq[u] = q;
       dd[u] = dist;
     }
@@ -204,7 +205,8 @@ __device__ __forceinline__ void build_chains(const typename SymType<S>::T *sym,
         }
       }
       const uint32_t mbits = __ballot_sync(kFull, mb);
-      if (lane == 0 && s0 + u < nslab) maybe[s0 + u] = mbits;
+      if (lane == 0 && s0 + u < nslab && GLZ_OK(s0 + u < (sm.mbar_off - sm.maybe_off) / 4))
+        maybe[s0 + u] = mbits;
     }
     __syncwarp();
   }
@@ -312,7 +314,7 @@ __device__ __forceinline__ bool literal_chunk(const typename SymType<S>::T *sym,
     }
 #pragma unroll
     for (uint32_t u = 0; u < kBloomGroup; ++u) {
-      old[u] = okk[u] ? atomicOr(&bm[widx[u]], mask[u]) : 0u;
+      old[u] = okk[u] && GLZ_OK(widx[u] < nwords) ? atomicOr(&bm[widx[u]], mask[u]) : 0u;
       __syncwarp();  // slab u's ORs before slab u+1's
     }
 #pragma unroll
@@ -366,6 +368,7 @@ __device__ __forceinline__ uint32_t extend_words(const uint8_t *in, uint32_t p,
                                                  uint32_t d, uint32_t cap) {
   constexpr uint32_t per = 4 / S;  // symbols per word
   uint32_t l = 0;
+  if (!GLZ_OK(d <= p)) return 0;
   while (l < cap) {
     const uint32_t x = bytes_at(in, (p + l) * S) ^ bytes_at(in, (p - d + l) * S);
     if (x) return min(cap, l + static_cast<uint32_t>(__ffs(x) - 1) / (8 * S));
@@ -393,9 +396,13 @@ __device__ __forceinline__ bool chain_match(const typename SymType<S>::T *sym,
   best = 0;
   bd = 0;
   uint32_t d = links.get(q), hops = 0, work = 0;
-  while (d != 0 && d <= A.W) {
+  while (d <= A.W) {
     if (best == lim) return true;
     if (hops >= kChainHops || work >= kChainWork) return false;
+    // the next link is loaded first, so that its latency overlaps the
+    // evaluation of this candidate (a link is >= 1; past the chain's end it
+    // reads as a distance that leaves the window)
+    const uint32_t step = GLZ_OK(d <= q) ? links.get(q - d) : 0x10000u;
     if (overlap || d >= A.m) {
       const uint32_t cap = overlap ? lim : min(lim, d);
       // only a candidate that agrees at index `best` can be longer
@@ -409,8 +416,6 @@ __device__ __forceinline__ bool chain_match(const typename SymType<S>::T *sym,
       }
     }
     ++hops;
-    const uint32_t step = links.get(q - d);
-    if (step == 0) break;
     d += step;
   }
   return true;
@@ -561,45 +566,44 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x, uint32_t lane,
   return incl - x;
 }
 
-// Step 3: greedy parse of one chunk into (flags, payload) staging.
+// Step 3: greedy parse of one chunk.  The walk decides the tokens and
+// records only the pointers: bit q of `pbits` marks a pointer at position q,
+// and the pointers' payload bytes (length, offset - 1) are listed in order
+// in `list` (1 + offB bytes each; the payload staging area holds any chunk's
+// list, since a pointer's bytes are part of the record's worst case).
+// Literals are not copied here: the record is written in one pass once its
+// place is known (emit_record, step 6).
 //
 // The marked positions are taken 32 at a time: lane i evaluates the i-th
 // next marked position with chain_match (exact).  The parse through the
 // batch is then a chain over lanes: from lane i (coding position q_i) it
 // moves to the first marked position at or after q_i + len (pointer of
 // len >= m) or q_i + 1 (literal); the unmarked positions in between are
-// literals and marked positions jumped over are covered.  A short serial
-// chase marks the visited lanes; two warp scans give every visited lane its
-// token index and payload offset, and the lanes write their tokens and
-// literal runs in parallel.
+// literals and marked positions jumped over are covered.  Pointer doubling
+// over the lanes' successors finds the visited lanes; warp sums give the
+// batch's token count and payload bytes (the local, first pass of the
+// two-pass prefix sum of section 3.2.2, per batch).
 template <int S, int NJ, bool WIDE>
 __device__ __forceinline__ void greedy_walk(const typename SymType<S>::T *sym,
                                             uint32_t k, const BufDesc &A,
                                             const CompressSmem &sm, const uint32_t *maybe,
-                                            const Links<WIDE> &links, uint8_t *flags,
-                                            uint8_t *pay, uint32_t lane,
+                                            const Links<WIDE> &links, uint32_t *pbits,
+                                            uint8_t *list, uint32_t lane,
                                             uint32_t &ntok_out, uint32_t &pay_out,
-                                            bool &sane) {
-  const uint8_t *in_bytes = reinterpret_cast<const uint8_t *>(sym);
-  uint32_t *flag_words = reinterpret_cast<uint32_t *>(flags);
-  const uint32_t pay_cap = sm.pay_bytes;
+                                            uint32_t &nptr_out, bool &sane) {
+  const uint32_t list_cap = sm.pay_bytes;
   sane = true;
   const uint32_t nw = (k + 31) / 32;
   const uint32_t tsz_match = 1 + A.offB;
-  uint32_t p = 0, ntok = 0, pb = 0;
+  for (uint32_t i = lane; i < nw; i += 32) pbits[i] = 0;
+  __syncwarp();
+  uint32_t p = 0, ntok = 0, pb = 0, np = 0;
   while (p < k) {
     const uint32_t q0 = next_marked(maybe, p, k);
     if (q0 > p) {  // run of literals
-      const uint32_t nb = (q0 - p) * S;
-      if (pb + nb > pay_cap) {  // cannot happen for a correct parse
-        sane = false;
-        break;
-      }
-      warp_copy_bytes(pay + pb, in_bytes + p * S, nb, lane);
-      pb += nb;
       ntok += q0 - p;
+      pb += (q0 - p) * S;
       p = q0;
-      __syncwarp();
       if (p >= k) break;
     }
     // batch: lane i <- i-th marked position >= p (32 mark words at a time,
@@ -669,69 +673,128 @@ __device__ __forceinline__ void greedy_walk(const typename SymType<S>::T *sym,
     const bool isv = (visited >> lane) & 1u;
     const uint32_t succ_pos = __shfl_sync(kFull, mypos, succ < 32 ? succ : lane);
     const uint32_t run_end = (lane == lastv) ? after : succ_pos;
-    const uint32_t run = isv ? run_end - nxt : 0u;
+    const uint32_t run = isv ? run_end - nxt : 0u;  // literals after this lane's token
     const bool is_match = isv && L >= A.m;
-    const uint32_t tsz = is_match ? tsz_match : S;
-    uint32_t tot_t, tot_b;
-    const uint32_t t_off = warp_excl_scan(isv ? 1u + run : 0u, lane, tot_t);
-    const uint32_t b_off = warp_excl_scan(isv ? tsz + run * S : 0u, lane, tot_b);
-    // consistency guard: the batch must stay inside the chunk and the
-    // staging area (always true for a correct parse)
-    if (pb + tot_b > pay_cap || ntok + tot_t > k || after > k || nxt_last > k) {
+    const uint32_t mmask = __ballot_sync(kFull, is_match);
+    const uint32_t tot_t = __reduce_add_sync(kFull, isv ? 1u + run : 0u);
+    const uint32_t tot_b =
+        __reduce_add_sync(kFull, isv ? (is_match ? tsz_match : S) + run * S : 0u);
+    const uint32_t nb = __popc(mmask);
+    // consistency guard: the batch must stay inside the chunk and the list
+    // (always true for a correct parse)
+    if (ntok + tot_t > k || after > k || nxt_last > k || tsz_match * (np + nb) > list_cap) {
       sane = false;
       break;
     }
-    if (is_match) {
-      const uint32_t t = ntok + t_off;
-      atomicOr(&flag_words[t >> 5], 1u << (t & 31));
-      uint8_t *o = pay + pb + b_off;
+    if (is_match && GLZ_OK(mypos < k && tsz_match * (np + __popc(mmask & lanemask_lt(lane)) + 1) <= list_cap)) {
+      uint8_t *o = list + tsz_match * (np + __popc(mmask & lanemask_lt(lane)));
       o[0] = static_cast<uint8_t>(L);
       o[1] = static_cast<uint8_t>((bd - 1) & 0xFF);
       if (A.offB == 2) o[2] = static_cast<uint8_t>((bd - 1) >> 8);
+      atomicOr(&pbits[mypos >> 5], 1u << (mypos & 31));
     }
-    // literal stretches: a visited literal whose previous visited lane is a
-    // pointer (or that is first) starts a run of literal symbols that lasts
-    // until the next visited pointer (or the end of the batch); its bytes
-    // are contiguous in both the chunk and the payload
-    const uint32_t mmask = __ballot_sync(kFull, is_match);
-    const uint32_t before = visited & lanemask_lt(lane);
-    const uint32_t pv = before ? 31u - __clz(before) : lane;
-    const bool starts = isv && !is_match && (before == 0 || ((mmask >> pv) & 1u));
-    const uint32_t later_m = mmask & ~((2u << lane) - 1u);  // pointers after this lane
-    const uint32_t nm = later_m ? __ffs(later_m) - 1 : lane;
-    const uint32_t nm_pos = __shfl_sync(kFull, mypos, nm);
-    const uint32_t s_end = later_m ? nm_pos : after;
-    const uint32_t sb = starts ? (s_end - mypos) * S : 0u;
-    if (starts && sb <= 32) {
-      uint8_t *o = pay + pb + b_off;
-      const uint8_t *src = in_bytes + mypos * S;
-      for (uint32_t i = 0; i < sb; ++i) o[i] = src[i];
-    }
-    // a pointer's own literal run (when the next visited lane is a pointer
-    // too, or it is the last) is copied by its lane or by the warp
-    const uint32_t rb = is_match ? run * S : 0u;
-    if (rb > 0 && rb <= 32) {
-      uint8_t *o = pay + pb + b_off + tsz;
-      const uint8_t *src = in_bytes + nxt * S;
-      for (uint32_t i = 0; i < rb; ++i) o[i] = src[i];
-    }
-    uint32_t longs = __ballot_sync(kFull, (starts && sb > 32) || rb > 32);
-    while (longs) {
-      const uint32_t i = __ffs(longs) - 1;
-      longs &= longs - 1;
-      const bool st_i = __shfl_sync(kFull, starts ? 1u : 0u, i) != 0;
-      const uint32_t o = __shfl_sync(kFull, st_i ? pb + b_off : pb + b_off + tsz, i);
-      const uint32_t src = __shfl_sync(kFull, st_i ? mypos * S : nxt * S, i);
-      const uint32_t nb = __shfl_sync(kFull, st_i ? sb : rb, i);
-      warp_copy_bytes(pay + o, in_bytes + src, nb, lane);
-    }
-    __syncwarp();
     ntok += tot_t;
     pb += tot_b;
+    np += nb;
     p = after;
   }
+  __syncwarp();
   ntok_out = ntok;
   pay_out = pb;
+  nptr_out = np;
+}
+
+// Step 6 for a record with pointers: the flags (to fdst), then the payload
+// and a stream-version-2 tail (to pdst), written in one pass over the
+// chunk's positions, 32 at a time (lane = position).  The destinations are
+// either the record's place (the stream, or a parking slot), or -- when a
+// pointer's payload bytes never exceed the input bytes it covers (S * m >=
+// 1 + offB) -- the shared memory it reads: the payload over the staged
+// chunk (a token's payload never starts after its position's input, so
+// nothing not yet read is overwritten) and the flags over the pointer
+// bitmap (token t's flag word is written only once the bitmap word of
+// position t has been read).  A position is a pointer start (its bit in
+// pbits; its payload bytes are the next entry of `list`), inside the
+// pointer that covers it (no token), or a literal (its S input bytes).  The
+// owning pointer of a position is the last pointer start at or before it
+// (a bit scan; one that began in an earlier round is carried).  Each
+// token's payload offset and index follow from popcounts over the round
+// (the local prefix sum of section 3.2.2); the flag bits of up to 32
+// tokens per round are gathered with two warp ORs.  Returns false when the
+// pass does not produce exactly (ntok, pay) (never for a correct walk).
+template <int S>
+__device__ __forceinline__ bool emit_record(uint8_t *fdst, uint8_t *payload, const uint8_t *inb,
+                                            uint32_t k, uint32_t tail, const uint32_t *pbits,
+                                            const uint8_t *list, uint32_t offB, uint32_t ntok,
+                                            uint32_t pay, uint32_t fcap, uint32_t pcap,
+                                            uint32_t lane) {
+  const uint32_t tsz = 1 + offB;
+  const uint32_t fb = (ntok + 7) / 8;
+  const uint32_t lt = lanemask_lt(lane), le = lt | (1u << lane);
+  uint32_t pbase = 0, tbase = 0, obase = 0;
+  uint32_t cend = 0;   // end of the last pointer started before this round
+  uint32_t fword = 0;  // flag bits of the current flag word (tokens 32*(tbase/32) ...)
+  for (uint32_t r0 = 0; r0 < k; r0 += 32) {
+    const uint32_t j = r0 + lane;
+    const bool act = j < k;
+    const uint32_t pw = pbits[r0 >> 5];
+    const bool ps = (pw >> lane) & 1u;
+    const uint32_t ord = obase + __popc(pw & lt);
+    uint32_t tok = 0;  // this lane's pointer token bytes
+    if (ps) {
+      const uint8_t *e = list + tsz * ord;
+      tok = e[0] | (static_cast<uint32_t>(e[1]) << 8) |
+            (offB == 2 ? static_cast<uint32_t>(e[2]) << 16 : 0u);
+    }
+    const uint32_t mb = pw & le;
+    const uint32_t ol = (31u - __clz(mb)) & 31u;
+    const uint32_t oend = __shfl_sync(kFull, j + (tok & 0xFFu), ol);
+    const uint32_t end_own = mb ? oend : cend;
+    cend = __shfl_sync(kFull, end_own, 31);
+    const bool lit = act && !ps && j >= end_own;
+    const uint32_t litm = __ballot_sync(kFull, lit);
+    const uint32_t tokm = litm | pw;
+    const uint32_t po = pbase + S * __popc(litm & lt) + tsz * __popc(pw & lt);
+    uint32_t v = 0;
+    if (lit) {
+      if constexpr (S == 1) v = inb[j];
+      else if constexpr (S == 2) v = reinterpret_cast<const uint16_t *>(inb)[j];
+      else v = reinterpret_cast<const uint32_t *>(inb)[j];
+    }
+    __syncwarp();  // every read of the round before any write (in place)
+    if (lit && GLZ_OK(po + S <= pcap)) {
+#pragma unroll
+      for (uint32_t i = 0; i < S; ++i) payload[po + i] = static_cast<uint8_t>(v >> (8 * i));
+    } else if (ps && GLZ_OK(po + tsz <= pcap)) {
+      payload[po] = static_cast<uint8_t>(tok);
+      payload[po + 1] = static_cast<uint8_t>(tok >> 8);
+      if (offB == 2) payload[po + 2] = static_cast<uint8_t>(tok >> 16);
+    }
+    // flag bits of this round's tokens (at most 32: words w0 and w0 + 1)
+    const uint32_t t = tbase + __popc(tokm & lt);
+    const uint32_t w0 = tbase >> 5;
+    const uint32_t lo = __reduce_or_sync(kFull, (ps && (t >> 5) == w0) ? 1u << (t & 31) : 0u);
+    const uint32_t hi = __reduce_or_sync(kFull, (ps && (t >> 5) != w0) ? 1u << (t & 31) : 0u);
+    fword |= lo;
+    const uint32_t ntb = tbase + __popc(tokm);
+    if ((ntb >> 5) != w0) {  // flag word w0 is complete
+      if (lane < 4 && GLZ_OK(4 * w0 + lane < fcap))
+        fdst[4 * w0 + lane] = static_cast<uint8_t>(fword >> (8 * lane));
+      fword = hi;
+    }
+    pbase += S * __popc(litm) + tsz * __popc(pw);
+    obase += __popc(pw);
+    tbase = ntb;
+    __syncwarp();
+  }
+  // the last, partial flag word (its bytes up to fb), the tail
+  const uint32_t w0 = tbase >> 5;
+  if (lane < 4 && 4 * w0 + lane < fb) fdst[4 * w0 + lane] = static_cast<uint8_t>(fword >> (8 * lane));
+  const uint8_t tb = lane < tail ? inb[k * S + lane] : 0;
+  __syncwarp();
+  if (lane < tail && GLZ_OK(pbase + lane < pcap)) payload[pbase + lane] = tb;
+  __syncwarp();
+  return tbase == ntok && pbase + tail == pay;
 }
 
 // Step 5: decoupled look-back (single-pass scan over chunks).  Status word:
@@ -807,14 +870,12 @@ __device__ __forceinline__ void warp_zero(uint8_t *dst, uint32_t n, uint32_t lan
 }
 
 // Step 6 for a chunk whose global offset is known: publish its inclusive
-// prefix, its index entry (every 64th chunk), the stream size (last chunk)
-// and copy its record (from shared staging or a parking slot; src1 ==
-// nullptr writes n1 zero bytes).
-__device__ __forceinline__ void place_record(const CompressArgs &A, const BufDesc &B,
-                                             uint32_t c, uint64_t excl, uint64_t rec,
-                                             const uint8_t *src1, uint32_t n1,
-                                             const uint8_t *src2, uint32_t n2,
-                                             bool data_ok, uint32_t lane) {
+// prefix, its index entry (every 64th chunk) and the stream size (last
+// chunk).  Returns where its record goes, or nullptr when it must not be
+// written (data not valid, or past the output capacity: kErrSmall).
+__device__ __forceinline__ uint8_t *place_meta(const CompressArgs &A, const BufDesc &B,
+                                               uint32_t c, uint64_t excl, uint64_t rec,
+                                               bool data_ok, uint32_t lane) {
   publish(A.status + B.gbase, c, kPrefix, excl + rec, lane);
   if (c % kIndexStride == 0) {
     uint8_t *idx = B.out + kHeaderBytes + static_cast<uint64_t>(kTableEntry) * B.nc +
@@ -823,12 +884,23 @@ __device__ __forceinline__ void place_record(const CompressArgs &A, const BufDes
   }
   const uint64_t dst = B.records_at + excl;
   if (c + 1 == B.nc && lane == 0) *B.out_bytes = dst + rec;
-  if (!data_ok) return;
+  if (!data_ok) return nullptr;
   if (dst + rec > B.cap) {
     if (lane == 0) atomicOr(A.err, kErrSmall);
-    return;
+    return nullptr;
   }
-  uint8_t *o = B.out + dst;
+  return B.out + dst;
+}
+
+// Step 6 with the record's bytes in memory: (src1, n1) then (src2, n2);
+// src1 == nullptr writes n1 zero bytes.
+__device__ __forceinline__ void place_record(const CompressArgs &A, const BufDesc &B,
+                                             uint32_t c, uint64_t excl, uint64_t rec,
+                                             const uint8_t *src1, uint32_t n1,
+                                             const uint8_t *src2, uint32_t n2,
+                                             bool data_ok, uint32_t lane) {
+  uint8_t *o = place_meta(A, B, c, excl, rec, data_ok, lane);
+  if (!o) return;
   if (src1) warp_copy(o, src1, n1, lane);
   else warp_zero(o, n1, lane);
   if (n2) warp_copy(o + n1, src2, n2, lane);
@@ -985,31 +1057,37 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
                           links, lane);
     for (uint32_t i = lane; i < (k + 31) / 32; i += 32) marked |= W.maybe[i];
   }
-  for (uint32_t i = lane; i < (k + 31) / 32; i += 32)
-    reinterpret_cast<uint32_t *>(W.flags)[i] = 0;
   __syncwarp();
 
-  // 3. greedy parse + local offsets.  With no marked position the parse is
-  // k literals and the payload is the staged chunk itself.
-  uint32_t ntok = k, pb = k * S;
+  // 3. greedy parse: the walk records the pointers (a bitmap in the flags
+  // area, their payload bytes listed in the payload area).  With no marked
+  // position, or no pointer, the record is k literals: zero flags, then the
+  // staged chunk itself.
+  uint32_t ntok = k, pb = k * S, np = 0;
   bool sane = true;
   const uint8_t *payload = W.inb;
+  uint32_t *pbits = reinterpret_cast<uint32_t *>(W.flags);
   if (__any_sync(kFull, marked != 0)) {
-    greedy_walk<S, NJ, WIDE>(sym, k, B, A.sm, W.maybe, links, W.flags, W.pay, lane, ntok, pb,
-                             sane);
-    payload = W.pay;
+    greedy_walk<S, NJ, WIDE>(sym, k, B, A.sm, W.maybe, links, pbits, W.pay, lane, ntok, pb,
+                             np, sane);
+    if (!sane) {
+      if (lane == 0) atomicOr(A.err, kErrInternal);
+      ntok = k;
+      pb = k * S;
+      np = 0;
+    }
   }
-  if (!sane && lane == 0) atomicOr(A.err, kErrInternal);
-  W.try_literal = payload == W.inb;  // no pointer in this chunk
+  // the record: 0 = zero flags + the staged chunk (all literals) or the
+  // chunk alone (stored); 1 = pointers, emitted at the record's place;
+  // 2 = pointers, emitted into shared memory (flags over the bitmap,
+  // payload over the staged chunk)
+  uint32_t kind = np != 0 ? 1u : 0u;
+  W.try_literal = kind == 0;
   // 4. stream version 2, last chunk: the 1..S-1 bytes after the last whole
   // symbol follow the tokens as they are (in the staged chunk they already
   // follow the k symbols)
   const uint32_t tail = bytes - k * S;
-  if (tail) {
-    if (payload != W.inb && lane < tail) W.pay[pb + lane] = W.inb[k * S + lane];
-    __syncwarp();
-    pb += tail;
-  }
+  pb += tail;
   uint32_t fb = (ntok + 7) / 8;
   if (B.version == 2 && fb + pb >= bytes) {
     // stream version 2: a record that would not be smaller than the chunk is
@@ -1018,13 +1096,34 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
     fb = 0;
     pb = bytes;
     payload = W.inb;
+    kind = 0;
+  }
+  if (kind == 1 && S * B.m >= 1 + B.offB) {
+    if (!emit_record<S>(W.flags, W.inb, W.inb, k, tail, pbits, W.pay, B.offB, ntok, pb,
+                        A.sm.pay_off - A.sm.flags_off, A.sm.prev_off - A.sm.in_off, lane) &&
+        lane == 0)
+      atomicOr(A.err, kErrInternal);
+    kind = 2;
   }
   const uint64_t rec = static_cast<uint64_t>(fb) + pb;
+  const bool data_ok = staged && sane;
+  // the record's bytes at o
+  auto write_record = [&](uint8_t *o) {
+    if (kind == 1) {
+      if (!emit_record<S>(o, o + fb, W.inb, k, tail, pbits, W.pay, B.offB, ntok, pb, fb, pb,
+                          lane) &&
+          lane == 0)
+        atomicOr(A.err, kErrInternal);
+    } else {
+      if (kind == 2) warp_copy(o, W.flags, fb, lane);
+      else warp_zero(o, fb, lane);
+      warp_copy(o + fb, payload, pb, lane);
+    }
+  };
 
   // 5. global offset: publish the aggregate at once, so that no other
-  // chunk waits on this warp; place the record now if the offset is
-  // known, else park it and move on (placed after a later chunk)
-  const bool data_ok = staged && sane;
+  // chunk waits on this warp; write the record now if the offset is known,
+  // else park it and move on (placed after a later chunk)
   if (c != 0) publish(status, c, kAgg, rec, lane);
   uint8_t *tab = B.out + kHeaderBytes + static_cast<uint64_t>(kTableEntry) * c;
   if (lane < 4)
@@ -1034,7 +1133,8 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
   drain_parked(A, W, false, lane);
   uint64_t excl;
   if (lookback_try(status, c, lane, excl)) {
-    place_record(A, B, c, excl, rec, W.flags, fb, payload, pb, data_ok, lane);
+    uint8_t *o = place_meta(A, B, c, excl, rec, data_ok, lane);
+    if (o) write_record(o);
   } else {
     const uint32_t free_mask =
         __ballot_sync(kFull, lane < A.park_slots && W.slot_c == kFreeSlot);
@@ -1043,12 +1143,9 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
       // a record of zero flags and the chunk's input (all literals), or of
       // the input alone (stored), is parked by reference
       // (not the last chunk: a copy may read up to 3 bytes past its source)
-      const bool by_ref = payload == W.inb && c + 1 < B.nc;
-      if (!by_ref) {
-        uint8_t *slot = W.slots + static_cast<uint64_t>(sidx) * A.park_slot_bytes;
-        warp_copy(slot, W.flags, fb, lane);
-        warp_copy(slot + fb, payload, pb, lane);
-      }
+      const bool by_ref = kind == 0 && c + 1 < B.nc;
+      if (!by_ref && GLZ_OK(rec <= A.park_slot_bytes))
+        write_record(W.slots + static_cast<uint64_t>(sidx) * A.park_slot_bytes);
       if (lane == sidx) {
         W.slot_c = c;
         W.slot_item = item;
@@ -1056,7 +1153,8 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
       }
     } else {
       const bool ok = lookback_wait(status, c, lane, A.err, excl, A.spin_limit);
-      place_record(A, B, c, excl, rec, W.flags, fb, payload, pb, data_ok && ok, lane);
+      uint8_t *o = place_meta(A, B, c, excl, rec, data_ok && ok, lane);
+      if (o) write_record(o);
     }
   }
   __syncwarp();
@@ -1078,11 +1176,12 @@ __global__ void __launch_bounds__(256) compress_kernel(const CompressArgs A) {
   init_warp_state(A, smem, W, lane);
   while (true) {
     const uint32_t c = take_ticket(A, lane);
-    if (c >= A.buf.nc) break;
+    if (c >= A.end_chunk) break;
     // one-byte links exactly when W <= 256, which is when NJ <= 8
     if (!compress_chunk<S, NJ, (NJ > 8)>(A, A.buf, 0, c, W, lane)) break;
   }
   drain_parked(A, W, true, lane);
+  if (lane == 0) checked_fold(A.err);
 }
 
 // Buffer holding global chunk g: the last item whose first chunk is <= g,
@@ -1141,6 +1240,7 @@ __global__ void __launch_bounds__(256) compress_batch_kernel(const CompressArgs 
     if (!ok) break;
   }
   drain_parked(A, W, true, lane);
+  if (lane == 0) checked_fold(A.err);
 }
 
 }  // namespace glz

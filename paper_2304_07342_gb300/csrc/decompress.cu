@@ -192,6 +192,7 @@ struct Slice {
   uint8_t *hi;              // high bytes of (offset - 1), or nullptr
   uint8_t *outb;            // output image, or nullptr (decode into the output)
   uint8_t *win;             // record window, or nullptr (read the record in place)
+  uint32_t win_bytes, out_bytes, mark_bytes;  // region sizes (bounds checks)
   uint32_t phase;           // parity of the next TMA completion on bar
 };
 
@@ -202,6 +203,9 @@ __device__ __forceinline__ Slice make_slice(uint8_t *ws, const DecodeLayout &L, 
   sl.hi = hi ? ws + L.hi_off : nullptr;
   sl.outb = L.staged ? ws + L.out_off : nullptr;
   sl.win = L.staged ? ws + L.win_off : nullptr;
+  sl.win_bytes = L.staged ? L.per_warp - L.win_off : 0;
+  sl.out_bytes = L.staged ? L.win_off - L.out_off : 0;
+  sl.mark_bytes = L.mark_bytes;
   sl.phase = 0;
   return sl;
 }
@@ -260,6 +264,7 @@ __device__ __forceinline__ bool decode_tokens(const Header &h, const uint8_t *fl
   np = __reduce_add_sync(kFull, np);
   if (S * (ntok - np) + tsz * np != pay_tok) return false;
   auto put = [&](uint32_t st, bool m, uint32_t off, uint32_t w) {
+    if (!GLZ_OK(st < k && st < sl.mark_bytes)) return;
     marks[st] = m ? 2 : 1;
     st_slot<S>(ob, st, m ? off - 1u : w, aligned);
     if (S == 1 && sl.hi && m) sl.hi[st] = static_cast<uint8_t>((off - 1u) >> 8);
@@ -289,8 +294,8 @@ __device__ __forceinline__ bool decode_tokens(const Header &h, const uint8_t *fl
       const uint32_t oA = S * (tA - nbA) + tsz * nbA, oB = S * (tB - nbB) + tsz * nbB;
       uint32_t wA = 0, wB = 0;
       if constexpr (STAGED) {
-        if (vA) wA = ld_u32_any(payload + oA);
-        if (vB) wB = ld_u32_any(payload + oB);
+        if (vA && GLZ_OK(oA < pay_tok)) wA = ld_u32_any(payload + oA);
+        if (vB && GLZ_OK(oB < pay_tok)) wB = ld_u32_any(payload + oB);
       } else {
         if (vA) wA = static_cast<uint32_t>(ld_le(payload + oA, mA ? tsz : S));
         if (vB) wB = static_cast<uint32_t>(ld_le(payload + oB, mB ? tsz : S));
@@ -352,7 +357,7 @@ __device__ __forceinline__ bool decode_tokens(const Header &h, const uint8_t *fl
         if (!__any_sync(kFull, moved)) break;
       }
     }
-    if (ptr) st_slot<S>(ob, j, ld_slot<S>(ob, f, aligned), aligned);
+    if (ptr && GLZ_OK(f < j)) st_slot<S>(ob, j, ld_slot<S>(ob, f, aligned), aligned);
     __syncwarp();
   }
   return true;
@@ -412,6 +417,7 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A, const Head
   const uint8_t *flags = in + rec_at;  // read in place when there is no window
   if (sl.win) {
     bool staged;
+    if (!GLZ_OK(fb + pay + 15 + 32 <= sl.win_bytes)) return true;
     flags = stage_record(in + rec_at, static_cast<uint32_t>(fb + pay), sl.win, sl.bar,
                          sl.phase, lane, staged);
     if (!staged) {
@@ -458,7 +464,7 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A, const Head
   }
   uint8_t *ob = sl.win ? sl.outb : dst;
   if (lane < tail) ob[static_cast<uint64_t>(k) * h.S + lane] = payload[pay_tok + lane];
-  if (sl.win) {
+  if (sl.win && GLZ_OK(bytes_c + 16 <= sl.out_bytes && chunk_at + bytes_c <= A.out_cap)) {
     __syncwarp();
     copy_s2g(dst, sl.outb, bytes_c, lane);
   }
@@ -515,6 +521,7 @@ __global__ void __launch_bounds__(1024, 1) decompress_kernel(const DecompressArg
   const uint32_t nwarps = gridDim.x * active;
   for (uint32_t c = gw; c < h.nc; c += nwarps)
     if (!decode_chunk(A, h, c, records_at, sl, lane)) break;
+  if (lane == 0) checked_fold(A.err);
 }
 
 // Batched decompression: chunks of all streams in order, grid-stride; each
@@ -587,6 +594,7 @@ __global__ void __launch_bounds__(1024, 1) decompress_batch_kernel(const Decompr
                       : nullptr;
     if (!decode_chunk(A, h, c, records_at, base, lane)) break;
   }
+  if (lane == 0) checked_fold(B.err);
 }
 
 cudaError_t launch_decompress_batch(DecompressBatchArgs B, int block, cudaStream_t stream) {

@@ -71,7 +71,8 @@ struct CompressArgs {
   uint32_t park_slots;         // slots per warp (<= 32)
   uint32_t park_slot_bytes;    // one worst-case record, 16-byte multiple
   uint32_t spin_limit;         // polls before a device wait gives up (kSpinLimit normally)
-  uint32_t first_ticket;       // first chunk handed out (0 normally; a test hook)
+  uint32_t first_ticket;       // first chunk handed out (0 normally)
+  uint32_t end_chunk;          // single buffer: chunks [first_ticket, end_chunk) are taken
 };
 
 // Placement of one shard stream inside a whole-input stream (lz_stitch).

@@ -11,6 +11,27 @@ namespace glz {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
+// Bounds-checked build (compiled with -DLZ_CHECKED): GLZ_OK(cond) guards a
+// shared- or global-memory access whose index the kernels compute; a false
+// condition records a violation in this translation unit's device word and
+// the access is skipped (no trap).  Each kernel folds the word into the
+// context's error word (kErrInternal, LZ_ERR_INTERNAL from lz_sync) when
+// it finishes.  In the normal build GLZ_OK is `true` and costs nothing.
+#ifdef LZ_CHECKED
+static __device__ unsigned int g_checked_violations;
+__device__ __forceinline__ bool checked_ok(bool ok) {
+  if (!ok) atomicAdd(&g_checked_violations, 1u);
+  return ok;
+}
+#define GLZ_OK(cond) ::glz::checked_ok(cond)
+__device__ __forceinline__ void checked_fold(uint32_t *err) {
+  if (*reinterpret_cast<volatile unsigned int *>(&g_checked_violations) != 0) atomicOr(err, kErrInternal);
+}
+#else
+#define GLZ_OK(cond) true
+__device__ __forceinline__ void checked_fold(uint32_t *) {}
+#endif
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

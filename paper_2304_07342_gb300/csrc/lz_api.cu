@@ -81,13 +81,12 @@ struct lz_ctx {
   uint32_t *d_err = nullptr;
   std::mutex mu;
   lz_test_hooks hooks{};    // test hooks (lz_set_test_hooks); all zero normally
-  // lz_compress_host: copy/compute streams, device slots, pinned staging
-  cudaStream_t hs[3] = {nullptr, nullptr, nullptr};
+  // lz_compress_host: copy and compression streams, events, device memory
+  // (the input, a size word, the stream when the output is not mapped)
+  cudaStream_t hs[2] = {nullptr, nullptr};
   cudaEvent_t hev[10] = {};
-  void *hdev = nullptr;       // device slots (input piece, piece stream, size)
+  void *hdev = nullptr;
   size_t hdev_bytes = 0;
-  void *hpin = nullptr;       // pinned: per slot a size and the piece's index entries
-  size_t hpin_bytes = 0;
 };
 
 namespace {
@@ -153,6 +152,29 @@ glz::CompressSmem compress_layout(const lz_params *p) {
   return sm;
 }
 
+// Warps per compression block and resident blocks per SM for a per-warp
+// slice of `per_warp` bytes: `want` warps per block (1, 2, 4 or 8) when
+// given, else the choice among 1, 2, 4 that keeps the most warps resident
+// under the per-SM shared-memory limit (each block also reserves some).
+// False when not even one block fits.
+bool block_shape(int64_t per_warp, int smem_per_sm, int smem_reserved, int smem_optin,
+                 uint32_t want, int *block, int64_t *blocks_per_sm) {
+  int64_t best_warps = 0;
+  for (int wpb = 1; wpb <= 8; wpb *= 2) {
+    if (want ? static_cast<uint32_t>(wpb) != want : wpb > kCompressWarps) continue;
+    const int64_t per_block = per_warp * wpb + smem_reserved;
+    if (per_block - smem_reserved > smem_optin) break;
+    int64_t blocks = smem_per_sm / per_block;
+    if (blocks > 32) blocks = 32;
+    if (blocks >= 1 && blocks * wpb > best_warps) {
+      best_warps = blocks * wpb;
+      *blocks_per_sm = blocks;
+      *block = 32 * wpb;
+    }
+  }
+  return best_warps > 0;
+}
+
 lz_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return LZ_OK;
   if (e == cudaErrorMemoryAllocation) return LZ_ERR_NOMEM;
@@ -188,7 +210,9 @@ lz_status reserve_scratch(lz_ctx *ctx, size_t bytes) {
 
 lz_status compress_locked(lz_ctx *ctx, const void *d_in, uint64_t n_bytes, const lz_params *p,
                           uint32_t match, uint32_t version, void *d_out, uint64_t out_cap,
-                          unsigned long long *out_bytes, cudaStream_t st);
+                          unsigned long long *out_bytes, cudaStream_t st, uint64_t c0 = 0,
+                          uint64_t c1 = ~0ull, bool clear_status = true,
+                          uint32_t warps_per_block = 0);
 
 }  // namespace
 
@@ -279,7 +303,6 @@ void lz_destroy(lz_ctx *ctx) {
   for (cudaEvent_t &e : ctx->hev)
     if (e) cudaEventDestroy(e);
   if (ctx->hdev) cudaFree(ctx->hdev);
-  if (ctx->hpin) cudaFreeHost(ctx->hpin);
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->d_err) cudaFree(ctx->d_err);
   delete ctx;
@@ -301,6 +324,9 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
     return LZ_ERR_INVALID_ARG;
   if (version != 1 && version != 2) return LZ_ERR_INVALID_ARG;
   if (match == LZ_MATCH_OVERLAP && version != 2) return LZ_ERR_INVALID_ARG;
+  if (opt && opt->warps_per_block && opt->warps_per_block != 1 && opt->warps_per_block != 2 &&
+      opt->warps_per_block != 4 && opt->warps_per_block != 8)
+    return LZ_ERR_INVALID_ARG;
   if (n_bytes > 0 && !d_in) return LZ_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(d_out_bytes) % 8 != 0) return LZ_ERR_INVALID_ARG;
   const uint32_t S = p->symbol_bytes, C = p->chunk_bytes;
@@ -314,7 +340,8 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
   std::lock_guard<std::mutex> lock(ctx->mu);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
   return compress_locked(ctx, d_in, n_bytes, p, match, version, d_out, out_cap,
-                         reinterpret_cast<unsigned long long *>(d_out_bytes), st);
+                         reinterpret_cast<unsigned long long *>(d_out_bytes), st, 0, ~0ull, true,
+                         opt ? opt->warps_per_block : 0u);
 }
 
 }  // extern "C"
@@ -322,12 +349,19 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
 namespace {
 
 // Enqueue one compression whose arguments lz_compress_ex has checked, with
-// the context's lock held and its device current.
+// the context's lock held and its device current: chunks [c0, c1) of the
+// buffer (all of them by default).  The look-back status words of every
+// chunk of the buffer are cleared when clear_status is set; a launch over
+// a later range of the same buffer keeps them (the ranges before it have
+// published their prefixes) and clears only the work counter.
 lz_status compress_locked(lz_ctx *ctx, const void *d_in, uint64_t n_bytes, const lz_params *p,
                           uint32_t match, uint32_t version, void *d_out, uint64_t out_cap,
-                          unsigned long long *out_bytes, cudaStream_t st) {
+                          unsigned long long *out_bytes, cudaStream_t st, uint64_t c0,
+                          uint64_t c1, bool clear_status, uint32_t warps_per_block) {
   const uint32_t S = p->symbol_bytes, C = p->chunk_bytes;
   const uint64_t nc = div_up(n_bytes, C);
+  if (c1 > nc) c1 = nc;
+  if (c0 >= c1 && nc > 0) return LZ_OK;
   const uint64_t records_at = glz::kHeaderBytes + glz::kTableEntry * nc +
                               8ull * div_up(nc, glz::kIndexStride);
   const uint32_t offB = off_bytes(p->window);
@@ -338,23 +372,13 @@ lz_status compress_locked(lz_ctx *ctx, const void *d_in, uint64_t n_bytes, const
 
   glz::CompressSmem sm = compress_layout(p);
   if (static_cast<int64_t>(sm.per_warp) > ctx->smem_optin) return LZ_ERR_INVALID_ARG;
-  // warps per block: the choice that keeps the most warps resident under the
-  // per-SM shared-memory limit (each block also reserves some shared memory)
   int block = 32;
-  int64_t best_warps = 0, best_blocks = 1;
-  for (int wpb = 1; wpb <= kCompressWarps; wpb *= 2) {
-    const int64_t per_block = static_cast<int64_t>(sm.per_warp) * wpb + ctx->smem_reserved;
-    if (per_block - ctx->smem_reserved > ctx->smem_optin) break;
-    int64_t blocks = ctx->smem_per_sm / per_block;
-    if (blocks > 32) blocks = 32;
-    if (blocks * wpb > best_warps) {
-      best_warps = blocks * wpb;
-      best_blocks = blocks;
-      block = 32 * wpb;
-    }
-  }
+  int64_t best_blocks = 1;
+  if (!block_shape(sm.per_warp, ctx->smem_per_sm, ctx->smem_reserved, ctx->smem_optin,
+                   warps_per_block, &block, &best_blocks))
+    return LZ_ERR_INVALID_ARG;
   const uint64_t wpb = block / 32;
-  uint64_t grid = div_up(nc, wpb);
+  uint64_t grid = div_up(c1 - c0, wpb);
   if (grid > static_cast<uint64_t>(best_blocks) * ctx->sms) grid = best_blocks * ctx->sms;
   // scratch: work counter, nc status words, parking slots of every warp
   const uint32_t slot_bytes = round16(div_up(C / S, 8) + sm.pay_bytes + 16);
@@ -363,7 +387,7 @@ lz_status compress_locked(lz_ctx *ctx, const void *d_in, uint64_t n_bytes, const
   const size_t need = park_at + static_cast<size_t>(slot_bytes) * kParkSlots * wpb * grid;
   lz_status s = reserve_scratch(ctx, need);
   if (s != LZ_OK) return s;
-  cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, status_end, st);
+  cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, clear_status ? status_end : kScratchHead, st);
   if (e != cudaSuccess) return LZ_ERR_CUDA;
 
   glz::CompressArgs A{};
@@ -396,7 +420,8 @@ lz_status compress_locked(lz_ctx *ctx, const void *d_in, uint64_t n_bytes, const
       static_cast<uint8_t *>(ctx->scratch) + kScratchHead);
   A.err = ctx->d_err;
   A.spin_limit = ctx->hooks.spin_limit ? ctx->hooks.spin_limit : glz::kSpinLimit;
-  A.first_ticket = ctx->hooks.first_chunk;
+  A.first_ticket = static_cast<uint32_t>(c0 + ctx->hooks.first_chunk);
+  A.end_chunk = static_cast<uint32_t>(c1);
   uint32_t nj = 1;
   while (32 * nj < p->window) nj *= 2;
   const unsigned g = static_cast<unsigned>(grid);
@@ -426,156 +451,98 @@ lz_status lz_compress_host(lz_ctx *ctx, const void *h_in, uint64_t n_bytes, cons
   if (out_cap < records_at) return LZ_ERR_BUFFER_TOO_SMALL;
   std::lock_guard<std::mutex> lock(ctx->mu);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
-  uint8_t *out = static_cast<uint8_t *>(h_out);
-  const uint8_t *in = static_cast<const uint8_t *>(h_in);
-  // the header, written on the host
-  {
-    uint8_t h[glz::kHeaderBytes] = {'G', 'L', 'Z', '1', 1, static_cast<uint8_t>(S),
-                                    static_cast<uint8_t>(off_bytes(p->window)),
-                                    static_cast<uint8_t>(p->min_match),
-                                    static_cast<uint8_t>(p->max_match)};
-    for (int i = 0; i < 4; ++i) {
-      h[12 + i] = static_cast<uint8_t>(C >> (8 * i));
-      h[16 + i] = static_cast<uint8_t>(p->window >> (8 * i));
-      h[20 + i] = static_cast<uint8_t>(nc >> (8 * i));
-    }
-    for (int i = 0; i < 8; ++i) h[24 + i] = static_cast<uint8_t>(n_bytes >> (8 * i));
-    std::memcpy(out, h, sizeof(h));
-  }
-  if (nc == 0) {
-    *h_out_bytes = records_at;
-    return LZ_OK;
-  }
-  // pieces of whole index superblocks, about 16 MiB, in three rotating slots
-  constexpr int kSlots = 3;
-  const uint64_t sb = glz::kIndexStride * static_cast<uint64_t>(C);
-  const uint64_t piece = std::max<uint64_t>(sb, ((16ull << 20) / sb) * sb);
-  const uint64_t npieces = div_up(n_bytes, piece);
-  const uint64_t piece_cap = (lz_compressed_bound(piece, p) + 255) & ~255ull;
-  const uint64_t slot_dev = ((piece + 255) & ~255ull) + piece_cap + 256;
-  const uint64_t piece_idx = div_up(piece / C, glz::kIndexStride);
-  const uint64_t slot_pin = 8 + 8 * piece_idx;
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
     if (!ctx->hs[i]) e = cudaStreamCreateWithFlags(&ctx->hs[i], cudaStreamNonBlocking);
   for (int i = 0; i < 10 && e == cudaSuccess; ++i)
     if (!ctx->hev[i]) e = cudaEventCreateWithFlags(&ctx->hev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) return cuda_status(e);
-  if (ctx->hdev_bytes < kSlots * slot_dev) {
+  // the output: written by the kernel in place when the host buffer is
+  // mapped into the device's address space (pinned memory), else through a
+  // device buffer copied out at the end
+  uint8_t *d_out = nullptr;
+  {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, h_out) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer)
+      d_out = static_cast<uint8_t *>(at.devicePointer);
+    cudaGetLastError();  // clear a lookup error of an unregistered pointer
+  }
+  // device memory: the input, a size word and (unmapped output) the stream
+  const uint64_t in_room = (n_bytes + 255) & ~255ull;
+  const uint64_t out_room = d_out ? 0 : ((std::min(out_cap, lz_compressed_bound(n_bytes, p)) +
+                                          255) & ~255ull);
+  const uint64_t want = in_room + 256 + out_room;
+  if (ctx->hdev_bytes < want) {
     if (ctx->hooks.fail_alloc) return LZ_ERR_NOMEM;
     if (ctx->hdev) cudaFree(ctx->hdev);
     ctx->hdev = nullptr;
     ctx->hdev_bytes = 0;
-    if ((e = cudaMalloc(&ctx->hdev, kSlots * slot_dev)) != cudaSuccess) return cuda_status(e);
-    ctx->hdev_bytes = kSlots * slot_dev;
+    if ((e = cudaMalloc(&ctx->hdev, want)) != cudaSuccess) return cuda_status(e);
+    ctx->hdev_bytes = want;
   }
-  if (ctx->hpin_bytes < kSlots * slot_pin) {
-    if (ctx->hooks.fail_alloc) return LZ_ERR_NOMEM;
-    if (ctx->hpin) cudaFreeHost(ctx->hpin);
-    ctx->hpin = nullptr;
-    ctx->hpin_bytes = 0;
-    if ((e = cudaMallocHost(&ctx->hpin, kSlots * slot_pin)) != cudaSuccess)
-      return cuda_status(e);
-    ctx->hpin_bytes = kSlots * slot_pin;
-  }
-  cudaStream_t s_in = ctx->hs[0], s_comp = ctx->hs[1], s_out = ctx->hs[2];
-  cudaEvent_t *ev_in = ctx->hev, *ev_comp = ctx->hev + 3, *ev_out = ctx->hev + 6;
+  uint8_t *d_in = static_cast<uint8_t *>(ctx->hdev);
+  auto *d_size = reinterpret_cast<unsigned long long *>(d_in + in_room);
+  const uint64_t cap = d_out ? out_cap : out_room;
+  if (!d_out) d_out = d_in + in_room + 256;
+  cudaStream_t s_in = ctx->hs[0], s_comp = ctx->hs[1];
   cudaEvent_t ev_start = ctx->hev[9];
-  uint8_t *dev = static_cast<uint8_t *>(ctx->hdev);
-  uint8_t *pin = static_cast<uint8_t *>(ctx->hpin);
-  auto slot_in = [&](int sl) { return dev + sl * slot_dev; };
-  auto slot_stream = [&](int sl) { return slot_in(sl) + ((piece + 255) & ~255ull); };
-  auto slot_size = [&](int sl) {
-    return reinterpret_cast<unsigned long long *>(slot_stream(sl) + piece_cap);
-  };
-  auto pin_size = [&](int sl) { return reinterpret_cast<uint64_t *>(pin + sl * slot_pin); };
-  auto pin_idx = [&](int sl) { return pin_size(sl) + 1; };
   if (cudaEventRecord(ev_start, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess ||
-      cudaStreamWaitEvent(s_in, ev_start, 0) != cudaSuccess)
+      cudaStreamWaitEvent(s_in, ev_start, 0) != cudaSuccess ||
+      cudaStreamWaitEvent(s_comp, ev_start, 0) != cudaSuccess)
     return LZ_ERR_CUDA;
   lz_status st = LZ_OK;
-  // copy-in and compression of piece i (slot i % 3; the slot's previous
-  // piece has been copied out once ev_out fires)
-  auto issue = [&](uint64_t i) -> lz_status {
-    const int sl = static_cast<int>(i % kSlots);
-    const uint64_t at = i * piece, len = std::min(piece, n_bytes - at);
-    if (i >= kSlots && cudaStreamWaitEvent(s_in, ev_out[sl], 0) != cudaSuccess) return LZ_ERR_CUDA;
-    if (cudaMemcpyAsync(slot_in(sl), in + at, len, cudaMemcpyHostToDevice, s_in) != cudaSuccess ||
-        cudaEventRecord(ev_in[sl], s_in) != cudaSuccess ||
-        cudaStreamWaitEvent(s_comp, ev_in[sl], 0) != cudaSuccess)
-      return LZ_ERR_CUDA;
-    lz_status r = compress_locked(ctx, slot_in(sl), len, p, LZ_MATCH_EXACT, 1, slot_stream(sl),
-                                  piece_cap, slot_size(sl), s_comp);
-    if (r != LZ_OK) return r;
-    const uint64_t pc = div_up(len, C), pidx = div_up(pc, glz::kIndexStride);
-    if (cudaMemcpyAsync(pin_size(sl), slot_size(sl), 8, cudaMemcpyDeviceToHost, s_comp) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(pin_idx(sl), slot_stream(sl) + glz::kHeaderBytes + 8 * pc, 8 * pidx,
-                        cudaMemcpyDeviceToHost, s_comp) != cudaSuccess ||
-        cudaEventRecord(ev_comp[sl], s_comp) != cudaSuccess)
-      return LZ_ERR_CUDA;
-    return LZ_OK;
-  };
-  uint64_t rec_base = 0;  // record bytes of the pieces before
-  bool fits = true;
-  for (uint64_t i = 0; i < std::min<uint64_t>(kSlots, npieces) && st == LZ_OK; ++i) st = issue(i);
-  for (uint64_t i = 0; i < npieces && st == LZ_OK; ++i) {
-    const int sl = static_cast<int>(i % kSlots);
-    const uint64_t at = i * piece, len = std::min(piece, n_bytes - at);
-    const uint64_t pc = div_up(len, C), pidx = div_up(pc, glz::kIndexStride);
-    const uint64_t cb = at / C;  // chunks before the piece (a multiple of 64)
-    const uint64_t p_records_at = glz::kHeaderBytes + 8 * pc + 8 * pidx;
-    if (cudaEventSynchronize(ev_comp[sl]) != cudaSuccess) {
-      st = LZ_ERR_CUDA;
-      break;
-    }
-    const uint64_t size = *pin_size(sl);
-    const uint64_t rec = size >= p_records_at ? size - p_records_at : 0;
-    fits = fits && records_at + rec_base + rec <= out_cap;
-    if (fits) {
-      for (uint64_t j = 0; j < pidx; ++j) {  // index entries, rebased
-        const uint64_t v = pin_idx(sl)[j] + rec_base;
-        uint8_t *d = out + glz::kHeaderBytes + 8 * nc + 8 * (cb / glz::kIndexStride + j);
-        for (int b = 0; b < 8; ++b) d[b] = static_cast<uint8_t>(v >> (8 * b));
-      }
-      if (cudaStreamWaitEvent(s_out, ev_comp[sl], 0) != cudaSuccess ||
-          cudaMemcpyAsync(out + glz::kHeaderBytes + 8 * cb, slot_stream(sl) + glz::kHeaderBytes,
-                          8 * pc, cudaMemcpyDeviceToHost, s_out) != cudaSuccess ||
-          cudaMemcpyAsync(out + records_at + rec_base, slot_stream(sl) + p_records_at, rec,
-                          cudaMemcpyDeviceToHost, s_out) != cudaSuccess) {
+  if (nc == 0) {
+    st = compress_locked(ctx, d_in, 0, p, LZ_MATCH_EXACT, 1, d_out, cap, d_size, s_comp);
+  } else {
+    // pieces of whole index superblocks, about 16 MiB: the copy of piece
+    // i + 1 overlaps the compression of piece i; a launch takes only its
+    // piece's chunks, and its look-back reaches into the pieces before it
+    const uint64_t sb = glz::kIndexStride * static_cast<uint64_t>(C);
+    const uint64_t piece = std::max<uint64_t>(sb, ((16ull << 20) / sb) * sb);
+    const uint64_t npieces = div_up(n_bytes, piece);
+    for (uint64_t i = 0; i < npieces && st == LZ_OK; ++i) {
+      const uint64_t at = i * piece, len = std::min(piece, n_bytes - at);
+      cudaEvent_t ev = ctx->hev[i % 8];
+      if (cudaMemcpyAsync(d_in + at, static_cast<const uint8_t *>(h_in) + at, len,
+                          cudaMemcpyHostToDevice, s_in) != cudaSuccess ||
+          cudaEventRecord(ev, s_in) != cudaSuccess ||
+          cudaStreamWaitEvent(s_comp, ev, 0) != cudaSuccess) {
         st = LZ_ERR_CUDA;
         break;
       }
-    } else if (cudaStreamWaitEvent(s_out, ev_comp[sl], 0) != cudaSuccess) {
-      st = LZ_ERR_CUDA;
-      break;
+      st = compress_locked(ctx, d_in, n_bytes, p, LZ_MATCH_EXACT, 1, d_out, cap, d_size, s_comp,
+                           at / C, (at + len) / C + ((at + len) % C ? 1 : 0), i == 0);
     }
-    if (cudaEventRecord(ev_out[sl], s_out) != cudaSuccess) {
-      st = LZ_ERR_CUDA;
-      break;
-    }
-    rec_base += rec;
-    if (i + kSlots < npieces) st = issue(i + kSlots);
   }
-  // finish the copies (also after an error: the slots must be idle)
+  uint64_t size = 0;
+  if (st == LZ_OK &&
+      (cudaMemcpyAsync(&size, d_size, 8, cudaMemcpyDeviceToHost, s_comp) != cudaSuccess ||
+       cudaStreamSynchronize(s_comp) != cudaSuccess))
+    st = LZ_ERR_CUDA;
   cudaStreamSynchronize(s_in);
   cudaStreamSynchronize(s_comp);
-  if (cudaStreamSynchronize(s_out) != cudaSuccess && st == LZ_OK) st = LZ_ERR_CUDA;
-  // device-side errors of the compressions, returned here (and cleared)
+  // device-side errors of this call, returned here (and cleared)
   uint32_t h = 0;
-  if (cudaMemcpy(&h, ctx->d_err, 4, cudaMemcpyDeviceToHost) != cudaSuccess && st == LZ_OK)
-    st = LZ_ERR_CUDA;
+  if (cudaMemcpyAsync(&h, ctx->d_err, 4, cudaMemcpyDeviceToHost, s_comp) != cudaSuccess ||
+      cudaStreamSynchronize(s_comp) != cudaSuccess) {
+    if (st == LZ_OK) st = LZ_ERR_CUDA;
+  }
   if (h) {
-    cudaMemset(ctx->d_err, 0, 4);
-    if (st == LZ_OK)
+    cudaMemsetAsync(ctx->d_err, 0, 4, s_comp);
+    cudaStreamSynchronize(s_comp);
+    if (st == LZ_OK && !(h == glz::kErrSmall))
       st = (h & glz::kErrInternal)  ? LZ_ERR_INTERNAL
            : (h & glz::kErrTimeout) ? LZ_ERR_TIMEOUT
            : (h & glz::kErrCorrupt) ? LZ_ERR_CORRUPT
                                     : LZ_ERR_BUFFER_TOO_SMALL;
   }
   if (st != LZ_OK) return st;
-  *h_out_bytes = records_at + rec_base;
-  return fits ? LZ_OK : LZ_ERR_BUFFER_TOO_SMALL;
+  *h_out_bytes = size;
+  if (size > out_cap) return LZ_ERR_BUFFER_TOO_SMALL;
+  if (out_room && cudaMemcpy(h_out, d_out, size, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LZ_ERR_CUDA;  // the stream went through a device buffer
+  return LZ_OK;
 }
 
 lz_status lz_decompressed_size(const void *d_in, uint64_t in_bytes,
@@ -779,18 +746,10 @@ extern "C" lz_status lz_compress_noalloc(const void *d_in, uint64_t n_bytes,
   const glz::CompressSmem sm = compress_layout(p);
   if (static_cast<int64_t>(sm.per_warp) > nd->smem_optin) return LZ_ERR_INVALID_ARG;
   int block = 32;
-  int64_t best_warps = 0, best_blocks = 1;
-  for (int wpb = 1; wpb <= kCompressWarps; wpb *= 2) {
-    const int64_t per_block = static_cast<int64_t>(sm.per_warp) * wpb + nd->smem_reserved;
-    if (per_block - nd->smem_reserved > nd->smem_optin) break;
-    int64_t blocks = nd->smem_per_sm / per_block;
-    if (blocks > 32) blocks = 32;
-    if (blocks * wpb > best_warps) {
-      best_warps = blocks * wpb;
-      best_blocks = blocks;
-      block = 32 * wpb;
-    }
-  }
+  int64_t best_blocks = 1;
+  if (!block_shape(sm.per_warp, nd->smem_per_sm, nd->smem_reserved, nd->smem_optin, 0, &block,
+                   &best_blocks))
+    return LZ_ERR_INVALID_ARG;
   uint64_t grid = div_up(nc, block / 32);
   if (grid > static_cast<uint64_t>(best_blocks) * nd->sms) grid = best_blocks * nd->sms;
   // the counter, the error word and the status words start at zero (one
@@ -821,6 +780,7 @@ extern "C" lz_status lz_compress_noalloc(const void *d_in, uint64_t n_bytes,
   A.ticket = reinterpret_cast<uint32_t *>(nd->scratch);
   A.err = reinterpret_cast<uint32_t *>(nd->scratch + 4);
   A.spin_limit = glz::kSpinLimit;
+  A.end_chunk = static_cast<uint32_t>(nc);
   A.status = reinterpret_cast<unsigned long long *>(nd->scratch + kNoAllocHead);
   uint32_t nj = 1;
   while (32 * nj < p->window) nj *= 2;
@@ -855,6 +815,7 @@ struct lz_batch {
   int planned = 0;                // 1 once a plan succeeded (runs allowed)
   int fail_alloc = 0;             // the context's injected allocation failure (test hook)
   uint32_t match = 0, version = 1;  // compression options of every plan
+  uint32_t warps_per_block = 0;
   cudaStream_t stream = nullptr;  // allocations and uploads are ordered on it
   DevBuf bufs[kBufCount];         // device allocations owned by the batch
   // compression
@@ -945,6 +906,7 @@ glz::CompressSmem compress_layout_max(const std::vector<lz_params> &ps) {
 
 lz_status batch_create_compress(lz_ctx *ctx, const lz_batch_item *items, uint32_t n,
                                 lz_batch *b, uint32_t match, uint32_t version) {
+  const uint32_t warps_per_block = b->warps_per_block;
   std::vector<glz::BufDesc> descs, empties;
   std::vector<uint64_t> bases;
   std::vector<lz_params> ps;
@@ -998,18 +960,10 @@ lz_status batch_create_compress(lz_ctx *ctx, const lz_batch_item *items, uint32_
   if (!ps.empty() && static_cast<int64_t>(sm.per_warp) > ctx->smem_optin)
     return LZ_ERR_INVALID_ARG;
   int block = 32;
-  int64_t best_warps = 0, best_blocks = 1;
-  for (int wpb = 1; !ps.empty() && wpb <= kCompressWarps; wpb *= 2) {
-    const int64_t per_block = static_cast<int64_t>(sm.per_warp) * wpb + ctx->smem_reserved;
-    if (per_block - ctx->smem_reserved > ctx->smem_optin) break;
-    int64_t blocks = ctx->smem_per_sm / per_block;
-    if (blocks > 32) blocks = 32;
-    if (blocks * wpb > best_warps) {
-      best_warps = blocks * wpb;
-      best_blocks = blocks;
-      block = 32 * wpb;
-    }
-  }
+  int64_t best_blocks = 1;
+  if (!ps.empty() && !block_shape(sm.per_warp, ctx->smem_per_sm, ctx->smem_reserved,
+                                  ctx->smem_optin, warps_per_block, &block, &best_blocks))
+    return LZ_ERR_INVALID_ARG;
   const uint64_t wpb = block / 32;
   uint64_t grid = std::max<uint64_t>(1, div_up(total, wpb));
   if (grid > static_cast<uint64_t>(best_blocks) * ctx->sms) grid = best_blocks * ctx->sms;
@@ -1180,6 +1134,8 @@ lz_status lz_batch_create_ex(lz_ctx *ctx, const lz_batch_item *items, uint32_t n
     return LZ_ERR_INVALID_ARG;
   if ((version != 1 && version != 2) || (match == LZ_MATCH_OVERLAP && version != 2))
     return LZ_ERR_INVALID_ARG;
+  const uint32_t wpb = opt ? opt->warps_per_block : 0u;
+  if (wpb && wpb != 1 && wpb != 2 && wpb != 4 && wpb != 8) return LZ_ERR_INVALID_ARG;
   *out = nullptr;
   std::lock_guard<std::mutex> lock(ctx->mu);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
@@ -1193,6 +1149,7 @@ lz_status lz_batch_create_ex(lz_ctx *ctx, const lz_batch_item *items, uint32_t n
              : match == LZ_MATCH_OVERLAP ? glz::kMatchOverlap
                                          : glz::kMatchExact;
   b->version = version;
+  b->warps_per_block = wpb;
   lz_status s = decompress ? batch_create_decompress(ctx, items, n_items, b)
                            : batch_create_compress(ctx, items, n_items, b, b->match, version);
   if (s != LZ_OK) {
@@ -1248,38 +1205,45 @@ void lz_batch_destroy(lz_batch *b, lz_stream_t stream) {
 
 lz_status lz_autotune(lz_ctx *ctx, const void *d_sample, uint64_t sample_bytes,
                       uint32_t symbol_bytes, lz_params *out) {
+  return lz_autotune_ex(ctx, d_sample, sample_bytes, symbol_bytes, out, nullptr, nullptr, 0,
+                        nullptr);
+}
+
+lz_status lz_autotune_ex(lz_ctx *ctx, const void *d_sample, uint64_t sample_bytes,
+                         uint32_t symbol_bytes, lz_params *out, uint32_t *out_warps_per_block,
+                         lz_tune_trial *trials_out, uint32_t max_trials, uint32_t *n_trials) {
   if (!ctx || !d_sample || !out) return LZ_ERR_INVALID_ARG;
   if (symbol_bytes != 1 && symbol_bytes != 2 && symbol_bytes != 4) return LZ_ERR_INVALID_ARG;
   sample_bytes -= sample_bytes % symbol_bytes;
   if (sample_bytes == 0) return LZ_ERR_INVALID_ARG;
-  const uint32_t Cs[3] = {2048, 4096, 8192};
-  const uint32_t Ws[3] = {64, 128, 256};
+  const uint32_t Cs[4] = {2048, 4096, 8192, 16384};
+  const uint32_t Ws[4] = {64, 128, 256, 512};
   const uint32_t m = symbol_bytes == 4 ? 2u : 3u;
-  struct Trial {
-    lz_params p;
-    double ratio, seconds;
-  };
-  std::vector<Trial> trials;
+  std::vector<lz_tune_trial> trials;
   uint64_t cap = 0;
   for (uint32_t C : Cs)
     for (uint32_t W : Ws) {
       lz_params p{symbol_bytes, C, W, m, 255};
       cap = std::max(cap, lz_compressed_bound(sample_bytes, &p));
-      trials.push_back({p, 0.0, 0.0});
+      trials.push_back({p, 0, 0.0, 0.0});
     }
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
   void *d_out = nullptr, *d_nb = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   lz_status s = LZ_OK;
-  if (cudaMalloc(&d_out, cap) != cudaSuccess || cudaMalloc(&d_nb, 8) != cudaSuccess ||
-      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+  if (ctx->hooks.fail_alloc || cudaMalloc(&d_out, cap) != cudaSuccess ||
+      cudaMalloc(&d_nb, 8) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
     s = LZ_ERR_NOMEM;
-  for (Trial &t : trials) {
-    if (s != LZ_OK) break;
-    for (int rep = 0; rep < 3 && s == LZ_OK; ++rep) {  // first run warms up
+  // one trial: three compressions (the first warms up), the mean of the
+  // last two, and the ratio
+  auto run = [&](lz_tune_trial &t) {
+    lz_options opt{LZ_MATCH_EXACT, 1, t.warps_per_block};
+    t.seconds = 0;
+    for (int rep = 0; rep < 3 && s == LZ_OK; ++rep) {
       cudaEventRecord(e0, nullptr);
-      s = lz_compress(ctx, d_sample, sample_bytes, &t.p, d_out, cap,
-                      static_cast<uint64_t *>(d_nb), nullptr);
+      s = lz_compress_ex(ctx, d_sample, sample_bytes, &t.params, &opt, d_out, cap,
+                         static_cast<uint64_t *>(d_nb), nullptr);
       cudaEventRecord(e1, nullptr);
       if (s == LZ_OK) s = lz_sync(ctx, nullptr);
       float ms = 0;
@@ -1290,26 +1254,59 @@ lz_status lz_autotune(lz_ctx *ctx, const void *d_sample, uint64_t sample_bytes,
     if (s == LZ_OK && cudaMemcpy(&size, d_nb, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
       s = LZ_ERR_CUDA;
     t.ratio = size ? static_cast<double>(sample_bytes) / size : 0.0;
+  };
+  for (lz_tune_trial &t : trials) {
+    if (s != LZ_OK) break;
+    run(t);
   }
+  lz_params best{};
+  uint32_t best_wpb = 0;
   if (s == LZ_OK) {
     // among the sets whose ratio is within 2% of the best ratio seen, the
     // smallest chunk that is within 10% of the fastest time (a smaller chunk
     // needs less shared memory per warp, which matters when buffers of other
     // kinds share a batched launch), the fastest among those
     double best_ratio = 0;
-    for (const Trial &t : trials) best_ratio = std::max(best_ratio, t.ratio);
+    for (const lz_tune_trial &t : trials) best_ratio = std::max(best_ratio, t.ratio);
     double fastest = 0;
-    for (const Trial &t : trials)
+    for (const lz_tune_trial &t : trials)
       if (t.ratio >= 0.98 * best_ratio && (fastest == 0 || t.seconds < fastest))
         fastest = t.seconds;
-    const Trial *pick = nullptr;
-    for (const Trial &t : trials) {
+    const lz_tune_trial *pick = nullptr;
+    for (const lz_tune_trial &t : trials) {
       if (t.ratio < 0.98 * best_ratio || t.seconds > 1.1 * fastest) continue;
-      if (!pick || t.p.chunk_bytes < pick->p.chunk_bytes ||
-          (t.p.chunk_bytes == pick->p.chunk_bytes && t.seconds < pick->seconds))
+      if (!pick || t.params.chunk_bytes < pick->params.chunk_bytes ||
+          (t.params.chunk_bytes == pick->params.chunk_bytes && t.seconds < pick->seconds))
         pick = &t;
     }
-    *out = pick->p;
+    best = pick->params;
+    // then the launch shape for it: warps per block 1, 2, 4, 8 (the stream
+    // is the same for all of them); the fastest, the library's own choice
+    // (0) on a tie within 2%
+    lz_tune_trial shape[5] = {{best, 0, 0, 0}, {best, 1, 0, 0}, {best, 2, 0, 0},
+                              {best, 4, 0, 0}, {best, 8, 0, 0}};
+    double fastest_shape = 0;
+    for (lz_tune_trial &t : shape) {
+      if (s != LZ_OK) break;
+      if (t.warps_per_block &&
+          static_cast<int64_t>(compress_layout(&best).per_warp) * t.warps_per_block >
+              ctx->smem_optin)
+        continue;  // this shape does not fit a block
+      run(t);
+      trials.push_back(t);
+      if (t.warps_per_block == 0 || t.seconds < 0.98 * fastest_shape) {
+        fastest_shape = t.seconds;
+        best_wpb = t.warps_per_block;
+      }
+    }
+  }
+  if (s == LZ_OK) {
+    *out = best;
+    if (out_warps_per_block) *out_warps_per_block = best_wpb;
+    if (trials_out)
+      for (uint32_t i = 0; i < std::min<size_t>(max_trials, trials.size()); ++i)
+        trials_out[i] = trials[i];
+    if (n_trials) *n_trials = static_cast<uint32_t>(trials.size());
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);

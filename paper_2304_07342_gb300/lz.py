@@ -36,7 +36,7 @@ _NAMES = {0: "LZ_OK", 1: "LZ_ERR_INVALID_ARG", 2: "LZ_ERR_BUFFER_TOO_SMALL",
 EXPORTS = ("lz_create", "lz_destroy", "lz_status_string", "lz_check_params",
            "lz_compressed_bound", "lz_compress", "lz_compress_ex", "lz_compress_host", "lz_decompressed_size",
            "lz_decompress", "lz_sync", "lz_compress_noalloc", "lz_batch_create",
-           "lz_batch_run", "lz_batch_update", "lz_batch_destroy", "lz_autotune", "lz_stitch", "lz_batch_create_ex",
+           "lz_batch_run", "lz_batch_update", "lz_batch_destroy", "lz_autotune", "lz_autotune_ex", "lz_stitch", "lz_batch_create_ex",
            "lz_select_params", "lz_huff_bound", "lz_huff_compress",
            "lz_huff_decompressed_size", "lz_huff_decompress", "lz_set_test_hooks")
 
@@ -54,12 +54,18 @@ class lz_params(ctypes.Structure):
 
 
 class lz_options(ctypes.Structure):
-    _fields_ = [("match", ctypes.c_uint32), ("version", ctypes.c_uint32)]
+    _fields_ = [("match", ctypes.c_uint32), ("version", ctypes.c_uint32),
+                ("warps_per_block", ctypes.c_uint32)]
 
 
 class lz_test_hooks(ctypes.Structure):
     _fields_ = [("spin_limit", ctypes.c_uint32), ("first_chunk", ctypes.c_uint32),
                 ("fail_alloc", ctypes.c_uint32)]
+
+
+class lz_tune_trial(ctypes.Structure):
+    _fields_ = [("params", lz_params), ("warps_per_block", ctypes.c_uint32),
+                ("seconds", ctypes.c_double), ("ratio", ctypes.c_double)]
 
 
 class lz_batch_item(ctypes.Structure):
@@ -133,6 +139,10 @@ def load(path: str = LIB_PATH):
     lib.lz_batch_destroy.restype = None
     lib.lz_autotune.argtypes = [vp, vp, u64, ctypes.c_uint32, pp]
     lib.lz_autotune.restype = i32
+    lib.lz_autotune_ex.argtypes = [vp, vp, u64, ctypes.c_uint32, pp, ctypes.POINTER(ctypes.c_uint32),
+                                   ctypes.POINTER(lz_tune_trial), ctypes.c_uint32,
+                                   ctypes.POINTER(ctypes.c_uint32)]
+    lib.lz_autotune_ex.restype = i32
     u32 = ctypes.c_uint32
     lib.lz_select_params.argtypes = [vp, vp, u64, u32, u32, u32, pp, vp]
     lib.lz_select_params.restype = i32
@@ -188,8 +198,9 @@ def lz_compress(ctx: int, d_in: int, n_bytes: int, p: Params, d_out: int,
 
 
 def lz_compress_ex(ctx: int, d_in: int, n_bytes: int, p: Params, d_out: int, out_cap: int,
-                   d_out_bytes: int, stream: int = 0, match: int = 0, version: int = 1) -> None:
-    opt = lz_options(match, version)
+                   d_out_bytes: int, stream: int = 0, match: int = 0, version: int = 1,
+                   warps_per_block: int = 0) -> None:
+    opt = lz_options(match, version, warps_per_block)
     _check(load().lz_compress_ex(ctx, d_in, n_bytes, ctypes.byref(p.c()), ctypes.byref(opt),
                                  d_out, out_cap, d_out_bytes, stream), "lz_compress_ex")
 
@@ -245,7 +256,7 @@ def lz_batch_create(ctx: int, items, decompress: bool = False, stream: int = 0,
         _check(load().lz_batch_create(ctx, arr, len(items), 1 if decompress else 0, stream,
                                       ctypes.byref(h)), "lz_batch_create")
     else:
-        opt = lz_options(match, version)
+        opt = lz_options(match, version, 0)
         _check(load().lz_batch_create_ex(ctx, arr, len(items), 1 if decompress else 0,
                                          ctypes.byref(opt), stream, ctypes.byref(h)),
                "lz_batch_create_ex")
@@ -280,6 +291,23 @@ def lz_autotune(ctx: int, d_sample: int, sample_bytes: int, symbol_bytes: int) -
     _check(load().lz_autotune(ctx, d_sample, sample_bytes, symbol_bytes, ctypes.byref(out)),
            "lz_autotune")
     return Params(out.symbol_bytes, out.chunk_bytes, out.window, out.min_match, out.max_match)
+
+
+def lz_autotune_ex(ctx: int, d_sample: int, sample_bytes: int, symbol_bytes: int):
+    """(Params, warps_per_block, trials): the choice of lz_autotune, the
+    launch shape for it, and every trial as a dict."""
+    out = lz_params()
+    wpb = ctypes.c_uint32()
+    arr = (lz_tune_trial * 64)()
+    n = ctypes.c_uint32()
+    _check(load().lz_autotune_ex(ctx, d_sample, sample_bytes, symbol_bytes, ctypes.byref(out),
+                                 ctypes.byref(wpb), arr, 64, ctypes.byref(n)), "lz_autotune_ex")
+    trials = [dict(S=t.params.symbol_bytes, C=t.params.chunk_bytes, W=t.params.window,
+                   m=t.params.min_match, M=t.params.max_match, warps_per_block=t.warps_per_block,
+                   ms=round(t.seconds * 1e3, 4), ratio=round(t.ratio, 4))
+              for t in arr[: min(64, n.value)]]
+    return (Params(out.symbol_bytes, out.chunk_bytes, out.window, out.min_match, out.max_match),
+            wpb.value, trials)
 
 
 def lz_select_params(ctx: int, d_sample: int, sample_bytes: int, dtype_bytes: int,
