@@ -18,6 +18,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblz.so")
+# the bounds-checked variant (-DLZ_CHECKED: computed shared/global indices
+# checked, violations reported as LZ_ERR_INTERNAL), built only on request
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "liblz_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
@@ -39,25 +43,28 @@ def _deps():
             [os.path.join(ROOT, "include", "lz.h"), __file__])
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    bdir = BUILD_CHECKED if checked else BUILD
+    if not force and up_to_date(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(bdir, exist_ok=True)
     procs = []
     objs = []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
         log = obj + ".log"
         objs.append(obj)
-        cmd = [nvcc, *ARCH, *FLAGS, "-Xptxas", "-v", "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *(["-DLZ_CHECKED"] if checked else []), "-Xptxas", "-v",
+               "-c", src, "-o", obj]
         procs.append((src, log, subprocess.Popen(
             cmd, stdout=open(log, "w"), stderr=subprocess.STDOUT)))
     failed = []
@@ -67,13 +74,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         msg = "\n".join(f"--- {s}\n{l}" for s, l in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     subprocess.check_call([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
         for _, log, _ in procs:
             sys.stdout.write(open(log).read())
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

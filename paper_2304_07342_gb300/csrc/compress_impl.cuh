@@ -1039,18 +1039,20 @@ __device__ __forceinline__ bool compress_chunk(const CompressArgs &A, const BufD
   }
   __syncwarp();
 
-  // 2. literal pre-check (when the payload area alone could hold a bitmap
-  // of >= 16 bits per position; the bitmap itself spans the links, flags
-  // and payload areas, contiguous and unused until the chains), else the
-  // candidate filter (hash table in the payload staging area)
-  const uint32_t bl = 31u - __clz(A.sm.pay_bytes / 4);  // bitmap words = 2^bl
+  // 2. literal pre-check (its bitmap spans the links, flags and payload
+  // areas, contiguous and unused until the chains; used for 2- and 4-byte
+  // symbols when that gives at least 8 bits per position -- for 1-byte
+  // symbols a key of three bytes repeats by chance often enough that the
+  // check mostly gives up), else the candidate filter (hash table in the
+  // payload area)
+  const uint32_t bm_words = (A.sm.maybe_off - A.sm.prev_off) / 4;
   bool literal = false;
   // (tried when this warp's previous chunk was all literals: on data with
   // repeats the check would only give up, so it is not tried again until a
   // chunk without a match comes by)
-  if (W.try_literal && bl >= 2 && (2u << bl) >= k)
-    literal = literal_chunk<S>(sym, k, B, reinterpret_cast<uint32_t *>(W.links_base),
-                               (A.sm.maybe_off - A.sm.prev_off) / 4, W.maybe, lane);
+  if (S >= 2 && W.try_literal && bm_words >= 16 && 4 * bm_words >= k)
+    literal = literal_chunk<S>(sym, k, B, reinterpret_cast<uint32_t *>(W.links_base), bm_words,
+                               W.maybe, lane);
   uint32_t marked = 0;
   if (!literal) {
     build_chains<S, WIDE>(sym, k, B, A.sm, reinterpret_cast<uint16_t *>(W.pay), W.maybe,

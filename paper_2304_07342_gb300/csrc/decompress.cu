@@ -124,16 +124,18 @@ __device__ __forceinline__ void st_slot(uint8_t *o, uint32_t j, uint32_t v, bool
   for (uint32_t i = 0; i < S; ++i) p[i] = static_cast<uint8_t>(v >> (8 * i));
 }
 
-// Copy record bytes [src, src + n) into the warp's window so that the copy
-// is 16-byte aligned on both sides: head and tail with plain loads, the
-// middle with one TMA bulk copy.  Returns the shared address of byte 0.
+// Copy record bytes [src, src + n) to the end of the warp's io area (16-byte
+// aligned, io_bytes long), ending at most kIoSlack bytes before it, so that
+// the copy is 16-byte aligned on both sides: head and tail with plain
+// loads, the middle with one TMA bulk copy.  Returns the shared address of
+// byte 0.
 __device__ __forceinline__ const uint8_t *stage_record(const uint8_t *src,
-                                                       uint32_t n, uint8_t *win,
-                                                       uint64_t *bar,
+                                                       uint32_t n, uint8_t *io,
+                                                       uint32_t io_bytes, uint64_t *bar,
                                                        uint32_t &phase,
                                                        uint32_t lane, bool &ok) {
   const uint32_t mis = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 15u);
-  uint8_t *dst = win + mis;
+  uint8_t *dst = io + ((io_bytes - kIoSlack - n - 15) & ~15u) + mis;
   const uint32_t head = min(n, (16u - mis) & 15u);
   const uint32_t bulk = (n - head) & ~15u;
   if (bulk && lane == 0) {
@@ -190,9 +192,10 @@ struct Slice {
   uint64_t *bar;
   uint8_t *marks;           // per position: 0 inside a token, 1 literal start, 2 pointer start
   uint8_t *hi;              // high bytes of (offset - 1), or nullptr
-  uint8_t *outb;            // output image, or nullptr (decode into the output)
-  uint8_t *win;             // record window, or nullptr (read the record in place)
-  uint32_t win_bytes, out_bytes, mark_bytes;  // region sizes (bounds checks)
+  uint8_t *fl;              // a copy of the record's flag bytes
+  uint8_t *io;              // output image + staged record, or nullptr (decode
+                            // into the output, read the record in place)
+  uint32_t io_bytes, flag_bytes, mark_bytes;  // region sizes
   uint32_t phase;           // parity of the next TMA completion on bar
 };
 
@@ -201,10 +204,10 @@ __device__ __forceinline__ Slice make_slice(uint8_t *ws, const DecodeLayout &L, 
   sl.bar = reinterpret_cast<uint64_t *>(ws);
   sl.marks = ws + L.marks_off;
   sl.hi = hi ? ws + L.hi_off : nullptr;
-  sl.outb = L.staged ? ws + L.out_off : nullptr;
-  sl.win = L.staged ? ws + L.win_off : nullptr;
-  sl.win_bytes = L.staged ? L.per_warp - L.win_off : 0;
-  sl.out_bytes = L.staged ? L.win_off - L.out_off : 0;
+  sl.fl = ws + L.flags_off;
+  sl.io = L.staged ? ws + L.io_off : nullptr;
+  sl.io_bytes = L.staged ? L.io_bytes : 0;
+  sl.flag_bytes = L.flag_bytes;
   sl.mark_bytes = L.mark_bytes;
   sl.phase = 0;
   return sl;
@@ -414,12 +417,12 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A, const Head
     if (lane == 0) atomicOr(A.err, kErrCorrupt);
     return true;
   }
-  const uint8_t *flags = in + rec_at;  // read in place when there is no window
-  if (sl.win) {
+  const uint8_t *flags = in + rec_at;  // read in place when there is no io area
+  if (sl.io) {
     bool staged;
-    if (!GLZ_OK(fb + pay + 15 + 32 <= sl.win_bytes)) return true;
-    flags = stage_record(in + rec_at, static_cast<uint32_t>(fb + pay), sl.win, sl.bar,
-                         sl.phase, lane, staged);
+    if (!GLZ_OK(fb + pay + kIoSlack + 15 <= sl.io_bytes)) return true;
+    flags = stage_record(in + rec_at, static_cast<uint32_t>(fb + pay), sl.io, sl.io_bytes,
+                         sl.bar, sl.phase, lane, staged);
     if (!staged) {
       if (lane == 0) atomicOr(A.err, kErrTimeout);
       return false;
@@ -428,8 +431,8 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A, const Head
   const uint8_t *payload = flags + fb;
   uint8_t *dst = A.out + chunk_at;
   if (stored) {
-    if (sl.win) {
-      copy_s2g(dst, payload, pay, lane);  // the window has slack past the record
+    if (sl.io) {
+      copy_s2g(dst, payload, pay, lane);  // the io area has slack past the record
     } else {
       for (uint32_t i = lane; i < pay; i += 32) dst[i] = payload[i];
     }
@@ -443,7 +446,7 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A, const Head
       if (lane == 0) atomicOr(A.err, kErrCorrupt);
       return true;
     }
-    if (sl.win) {
+    if (sl.io) {
       copy_s2g(dst, payload, pay, lane);
     } else {
       for (uint32_t i = lane; i < pay; i += 32) dst[i] = payload[i];
@@ -451,9 +454,16 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A, const Head
     return true;
   }
   const uint32_t pay_tok = pay - tail;  // the tokens' payload; the tail follows it
+  // the tail bytes, read before the output image may grow over the record
+  const uint8_t tb = lane < tail ? payload[pay_tok + lane] : 0;
   bool ok;
-  if (sl.win) {
-    ok = decode_tokens_s<true>(h, flags, payload, ntok, pay_tok, k, sl.outb, true, sl, lane);
+  if (sl.io) {
+    // the flag bytes are copied out first: the output image grows from the
+    // start of the io area towards the record's flags
+    if (!GLZ_OK(fb + 8 <= sl.flag_bytes)) return true;
+    for (uint32_t i = lane; i < fb; i += 32) sl.fl[i] = flags[i];
+    __syncwarp();
+    ok = decode_tokens_s<true>(h, sl.fl, payload, ntok, pay_tok, k, sl.io, true, sl, lane);
   } else {
     const bool aligned = A.out_aligned != 0 && (h.C % 4) == 0;
     ok = decode_tokens_s<false>(h, flags, payload, ntok, pay_tok, k, dst, aligned, sl, lane);
@@ -462,11 +472,11 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A, const Head
     if (lane == 0) atomicOr(A.err, kErrCorrupt);
     return true;
   }
-  uint8_t *ob = sl.win ? sl.outb : dst;
-  if (lane < tail) ob[static_cast<uint64_t>(k) * h.S + lane] = payload[pay_tok + lane];
-  if (sl.win && GLZ_OK(bytes_c + 16 <= sl.out_bytes && chunk_at + bytes_c <= A.out_cap)) {
+  uint8_t *ob = sl.io ? sl.io : dst;
+  if (lane < tail) ob[static_cast<uint64_t>(k) * h.S + lane] = tb;
+  if (sl.io && GLZ_OK(bytes_c + 16 <= sl.io_bytes && chunk_at + bytes_c <= A.out_cap)) {
     __syncwarp();
-    copy_s2g(dst, sl.outb, bytes_c, lane);
+    copy_s2g(dst, sl.io, bytes_c, lane);
   }
   __syncwarp();
   return true;
@@ -476,7 +486,7 @@ __device__ __forceinline__ bool decode_chunk(const DecompressArgs &A, const Head
 __device__ __forceinline__ DecodeLayout layout_of(const Header &h, uint64_t budget) {
   const uint64_t k = h.C / h.S;
   return decode_layout(k, h.C, decode_record_bound(k, h.S, h.offB, h.m), h.S == 1 && h.offB == 2,
-                       budget);
+                       h.S * h.m >= 1 + h.offB, budget);
 }
 
 }  // namespace
@@ -570,12 +580,18 @@ __global__ void __launch_bounds__(1024, 1) decompress_batch_kernel(const Decompr
     // the header must still be the one the plan sized the slices for
     const uint64_t kh = ok ? h.C / h.S : 0;
     const bool need_hi = ok && h.S == 1 && h.offB == 2;
+    // the io area: a stream whose pointers may outgrow their symbols needs
+    // the output image and the record side by side
+    auto fits_io = [](const DecodeLayout &L, const Header &hh, uint64_t kk) {
+      const uint64_t c16 = ((hh.C + 15) & ~15ull) + 16;
+      const uint64_t r16 = (decode_record_bound(kk, hh.S, hh.offB, hh.m) + 15) & ~15ull;
+      const bool sh = hh.S * hh.m >= 1 + hh.offB;
+      return (sh ? (c16 > r16 ? c16 : r16) : c16 + r16) + 32 + kIoSlack <= L.io_bytes;
+    };
     const bool fits = ok && h.nc == it.nc && kh <= B.lay.mark_bytes &&
-                      (!need_hi || B.lay.out_off - B.lay.hi_off >= kh) &&
-                      (!B.lay.staged ||
-                       (h.C + 16 <= B.lay.win_off - B.lay.out_off &&
-                        decode_record_bound(kh, h.S, h.offB, h.m) + 64 <=
-                            B.lay.per_warp - B.lay.win_off)) &&
+                      (!need_hi || B.lay.io_off - B.lay.hi_off >= kh) &&
+                      (kh + 7) / 8 + 8 <= B.lay.flag_bytes &&
+                      (!B.lay.staged || fits_io(B.lay, h, kh)) &&
                       records_at <= it.in_bytes && h.n <= it.out_cap;
     if (!fits) {
       if (lane == 0) atomicOr(B.err, h.n > it.out_cap && ok ? kErrSmall : kErrCorrupt);

@@ -115,17 +115,24 @@ struct DecItem {
 
 // Per-warp shared-memory slice of the decoder (byte offsets, 16-byte
 // aligned): an mbarrier, one mark byte per position of the chunk (0 inside
-// a token, 1 where a literal starts, 2 where a pointer starts), the high
-// bytes of (offset - 1) when one-byte symbols carry two-byte offsets, then
-// -- when they fit -- the chunk's output and a window for its record.
-// Without them (`staged` false) a warp decodes straight into the output
-// buffer and reads the record in place.
+// a token, 1 where a literal starts, 2 where a pointer starts), a copy of
+// the record's flag bytes, the high bytes of (offset - 1) when one-byte
+// symbols carry two-byte offsets, then -- when they fit -- the io area:
+// the chunk's output image from its start, with the record staged at its
+// end.  When no pointer takes more payload bytes than the symbols it
+// covers (S * m >= 1 + offB for every stream; `shared`), the output
+// written so far never reaches a payload byte not yet read, so the area
+// only needs room for the larger of the two; otherwise it holds both side
+// by side.  Without the io area (`staged` false) a warp decodes straight
+// into the output buffer and reads the record in place.
 struct DecodeLayout {
   uint32_t marks_off;  // mark bytes, a multiple of 32
   uint32_t mark_bytes;
+  uint32_t flags_off;  // flag bytes of one record (+ 16 slack)
+  uint32_t flag_bytes;
   uint32_t hi_off;     // k bytes (one-byte symbols, two-byte offsets) or none
-  uint32_t out_off;    // C bytes + 16 slack
-  uint32_t win_off;    // largest record + 64 slack
+  uint32_t io_off;     // output image + staged record
+  uint32_t io_bytes;
   uint32_t per_warp;
   uint32_t staged;
 };
@@ -138,23 +145,32 @@ __host__ __device__ inline uint64_t decode_record_bound(uint64_t k, uint32_t S, 
   return (k + 7) / 8 + static_cast<uint64_t>(S) * k + extra * (k / m) + (S - 1);
 }
 
+// Slack of the io area past the staged record (its end is at most this
+// many bytes before the area's end, minus 15 for alignment).
+constexpr uint32_t kIoSlack = 64;
+
 // Slice for chunks of at most `kmax` symbols and `cmax` bytes whose records
 // are at most `rmax` bytes; the full slice when `budget` bytes hold it,
-// else the bitmaps alone.
+// else without the io area.
 __host__ __device__ inline DecodeLayout decode_layout(uint64_t kmax, uint64_t cmax,
-                                                      uint64_t rmax, bool hi, uint64_t budget) {
+                                                      uint64_t rmax, bool hi, bool shared,
+                                                      uint64_t budget) {
   DecodeLayout L{};
   uint64_t at = 16;  // mbarrier
   L.marks_off = static_cast<uint32_t>(at);
   L.mark_bytes = static_cast<uint32_t>((kmax + 31) & ~31ull);
   at += L.mark_bytes;
+  L.flags_off = static_cast<uint32_t>(at);
+  L.flag_bytes = static_cast<uint32_t>(((kmax + 7) / 8 + 15) & ~15ull) + 16;
+  at += L.flag_bytes;
   L.hi_off = static_cast<uint32_t>(at);
   if (hi) at += (kmax + 15) & ~15ull;
   const uint64_t base = at;
-  L.out_off = static_cast<uint32_t>(at);
-  at += ((cmax + 15) & ~15ull) + 16;
-  L.win_off = static_cast<uint32_t>(at);
-  at += ((rmax + 15) & ~15ull) + 64;
+  L.io_off = static_cast<uint32_t>(at);
+  const uint64_t c16 = ((cmax + 15) & ~15ull) + 16, r16 = (rmax + 15) & ~15ull;
+  L.io_bytes = static_cast<uint32_t>((shared ? (c16 > r16 ? c16 : r16) : c16 + r16) + 32 +
+                                     kIoSlack);
+  at += L.io_bytes;
   L.staged = at <= budget;
   if (!L.staged) at = base;
   L.per_warp = static_cast<uint32_t>(at);

@@ -137,7 +137,23 @@ glz::CompressSmem compress_layout(const lz_params *p) {
   sm.flags_off = at;
   at += round16(div_up(k, 32) * 4);
   sm.pay_off = at;
-  const uint32_t pay_region = round16(pay_bytes + 16);
+  // The payload area holds the hash table while the chains are built, then
+  // the pointer list of the walk (1 + offB bytes per pointer, at most k / m
+  // of them); records are emitted in place or at their destination.  For 1-
+  // and 2-byte symbols it takes a table of half as many buckets as the
+  // chunk has positions: less shared memory per warp, more warps resident.
+  // For 4-byte symbols it keeps the size of a worst-case payload, which the
+  // literal pre-check's Bloom filter uses (with links and flags) to hold
+  // about 10 bits per position.
+  uint32_t pay_region = round16(pay_bytes + 16);
+  if (S <= 2) {
+    uint32_t lgk = 1;
+    while ((1u << lgk) < k) ++lgk;
+    const uint32_t lgt = lgk > 4 ? lgk - 1 : 4;
+    const uint64_t list = (1ull + offB) * (k / p->min_match);
+    const uint64_t table = 2ull << lgt;
+    pay_region = round16((list > table ? list : table) + 16);
+  }
   sm.pay_bytes = pay_region;
   at += pay_region;
   sm.maybe_off = at;
@@ -381,7 +397,8 @@ lz_status compress_locked(lz_ctx *ctx, const void *d_in, uint64_t n_bytes, const
   uint64_t grid = div_up(c1 - c0, wpb);
   if (grid > static_cast<uint64_t>(best_blocks) * ctx->sms) grid = best_blocks * ctx->sms;
   // scratch: work counter, nc status words, parking slots of every warp
-  const uint32_t slot_bytes = round16(div_up(C / S, 8) + sm.pay_bytes + 16);
+  const uint32_t slot_bytes =
+      round16(record_bound(C / S, S, off_bytes(p->window), p->min_match) + S + 16);
   const size_t status_end = kScratchHead + 8ull * nc;
   const size_t park_at = (status_end + 255) & ~static_cast<size_t>(255);
   const size_t need = park_at + static_cast<size_t>(slot_bytes) * kParkSlots * wpb * grid;
@@ -967,7 +984,13 @@ lz_status batch_create_compress(lz_ctx *ctx, const lz_batch_item *items, uint32_
   const uint64_t wpb = block / 32;
   uint64_t grid = std::max<uint64_t>(1, div_up(total, wpb));
   if (grid > static_cast<uint64_t>(best_blocks) * ctx->sms) grid = best_blocks * ctx->sms;
-  const uint32_t slot_bytes = round16(div_up(kmax, 8) + sm.pay_bytes + 16);
+  uint64_t rb_max = 0;  // a parking slot holds any item's largest record
+  for (const lz_params &q : ps)
+    rb_max = std::max<uint64_t>(rb_max, record_bound(q.chunk_bytes / q.symbol_bytes,
+                                                     q.symbol_bytes, off_bytes(q.window),
+                                                     q.min_match) +
+                                            q.symbol_bytes);
+  const uint32_t slot_bytes = round16(rb_max + 16);
   const size_t status_end = kScratchHead + 8ull * total;
   const size_t park_at = (status_end + 255) & ~static_cast<size_t>(255);
   const size_t scratch = park_at + static_cast<size_t>(slot_bytes) * kParkSlots * wpb * grid;
@@ -1045,7 +1068,7 @@ lz_status batch_create_decompress(lz_ctx *ctx, const lz_batch_item *items, uint3
   std::vector<glz::DecItem> descs, empties;
   std::vector<uint64_t> bases;
   uint64_t total = 0, max_rec = 0, max_k = 1, max_c = 16;
-  bool need_hi = false;
+  bool need_hi = false, shared = true;
   for (uint32_t i = 0; i < n; ++i) {
     const uint8_t *h = &hdr[static_cast<size_t>(i) * 32];
     lz_params p;
@@ -1088,11 +1111,13 @@ lz_status batch_create_decompress(lz_ctx *ctx, const lz_batch_item *items, uint3
     max_k = std::max(max_k, k);
     max_c = std::max<uint64_t>(max_c, p.chunk_bytes);
     need_hi = need_hi || (p.symbol_bytes == 1 && off_bytes(p.window) == 2);
+    shared = shared && p.symbol_bytes * p.min_match >= 1 + off_bytes(p.window);
     max_rec = std::max(max_rec, glz::decode_record_bound(k, p.symbol_bytes,
                                                          off_bytes(p.window), p.min_match));
   }
   const uint32_t budget = decode_block_smem(ctx);
-  const glz::DecodeLayout lay = glz::decode_layout(max_k, max_c, max_rec, need_hi, budget);
+  const glz::DecodeLayout lay =
+      glz::decode_layout(max_k, max_c, max_rec, need_hi, shared, budget);
   if (lay.per_warp > budget) return LZ_ERR_INVALID_ARG;
   const uint64_t warps = std::min<uint64_t>(32, budget / lay.per_warp);
   const glz::DecItem *d_items = nullptr, *d_empty = nullptr;
