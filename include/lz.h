@@ -174,7 +174,7 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
  * lz_compress of the same bytes, for callers whose data lives on the host.
  * h_in (n_bytes) and h_out (capacity out_cap) are host buffers.  The input
  * is copied to the device in pieces of whole index superblocks (64 chunks,
- * about 16 MiB a piece), and each piece is compressed by a launch over its
+ * about 64 MiB a piece), and each piece is compressed by a launch over its
  * own chunks as soon as it has arrived, while the next piece is copied:
  * chunks are independent (section 3.3.1) and the look-back of a piece's
  * first chunks reaches into the pieces before it, which are complete.
@@ -313,7 +313,7 @@ void lz_batch_destroy(lz_batch *batch, lz_stream_t stream);
 /* Choose chunk_bytes and window for data of `symbol_bytes`-byte symbols from
  * timed trial compressions of a device-resident sample: among C in {2048,
  * 4096, 8192, 16384} and W in {64, 128, 256, 512} whose compression ratio
- * is within 2% of the best ratio found, the smallest C that is within 10%
+ * is within 5% of the best ratio found, the smallest C that is within 10%
  * of the fastest time (less shared memory per warp, which helps a batched
  * launch over buffers of several kinds), then the fastest; min_match 3 (2
  * for 4-byte symbols), max_match 255.  The choice changes the stream (it is

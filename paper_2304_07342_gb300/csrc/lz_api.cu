@@ -140,8 +140,9 @@ glz::CompressSmem compress_layout(const lz_params *p) {
   // The payload area holds the hash table while the chains are built, then
   // the pointer list of the walk (1 + offB bytes per pointer, at most k / m
   // of them); records are emitted in place or at their destination.  For 1-
-  // and 2-byte symbols it takes a table of half as many buckets as the
-  // chunk has positions: less shared memory per warp, more warps resident.
+  // and 2-byte symbols it takes a table of a quarter as many buckets as the
+  // chunk has positions (or the list, if larger): less shared memory per
+  // warp, more warps resident.
   // For 4-byte symbols it keeps the size of a worst-case payload, which the
   // literal pre-check's Bloom filter uses (with links and flags) to hold
   // about 10 bits per position.
@@ -149,7 +150,7 @@ glz::CompressSmem compress_layout(const lz_params *p) {
   if (S <= 2) {
     uint32_t lgk = 1;
     while ((1u << lgk) < k) ++lgk;
-    const uint32_t lgt = lgk > 4 ? lgk - 1 : 4;
+    const uint32_t lgt = lgk > 6 ? lgk - 2 : 4;
     const uint64_t list = (1ull + offB) * (k / p->min_match);
     const uint64_t table = 2ull << lgt;
     pay_region = round16((list > table ? list : table) + 16);
@@ -512,11 +513,13 @@ lz_status lz_compress_host(lz_ctx *ctx, const void *h_in, uint64_t n_bytes, cons
   if (nc == 0) {
     st = compress_locked(ctx, d_in, 0, p, LZ_MATCH_EXACT, 1, d_out, cap, d_size, s_comp);
   } else {
-    // pieces of whole index superblocks, about 16 MiB: the copy of piece
+    // pieces of whole index superblocks, about 64 MiB: the copy of piece
     // i + 1 overlaps the compression of piece i; a launch takes only its
     // piece's chunks, and its look-back reaches into the pieces before it
+    // (4 MiB pieces measured 26 % slower end to end, 16 MiB 3 %: each
+    // piece costs a launch and an event wait)
     const uint64_t sb = glz::kIndexStride * static_cast<uint64_t>(C);
-    const uint64_t piece = std::max<uint64_t>(sb, ((16ull << 20) / sb) * sb);
+    const uint64_t piece = std::max<uint64_t>(sb, ((64ull << 20) / sb) * sb);
     const uint64_t npieces = div_up(n_bytes, piece);
     for (uint64_t i = 0; i < npieces && st == LZ_OK; ++i) {
       const uint64_t at = i * piece, len = std::min(piece, n_bytes - at);
@@ -1287,7 +1290,7 @@ lz_status lz_autotune_ex(lz_ctx *ctx, const void *d_sample, uint64_t sample_byte
   lz_params best{};
   uint32_t best_wpb = 0;
   if (s == LZ_OK) {
-    // among the sets whose ratio is within 2% of the best ratio seen, the
+    // among the sets whose ratio is within 5% of the best ratio seen, the
     // smallest chunk that is within 10% of the fastest time (a smaller chunk
     // needs less shared memory per warp, which matters when buffers of other
     // kinds share a batched launch), the fastest among those
@@ -1295,11 +1298,11 @@ lz_status lz_autotune_ex(lz_ctx *ctx, const void *d_sample, uint64_t sample_byte
     for (const lz_tune_trial &t : trials) best_ratio = std::max(best_ratio, t.ratio);
     double fastest = 0;
     for (const lz_tune_trial &t : trials)
-      if (t.ratio >= 0.98 * best_ratio && (fastest == 0 || t.seconds < fastest))
+      if (t.ratio >= 0.95 * best_ratio && (fastest == 0 || t.seconds < fastest))
         fastest = t.seconds;
     const lz_tune_trial *pick = nullptr;
     for (const lz_tune_trial &t : trials) {
-      if (t.ratio < 0.98 * best_ratio || t.seconds > 1.1 * fastest) continue;
+      if (t.ratio < 0.95 * best_ratio || t.seconds > 1.1 * fastest) continue;
       if (!pick || t.params.chunk_bytes < pick->params.chunk_bytes ||
           (t.params.chunk_bytes == pick->params.chunk_bytes && t.seconds < pick->seconds))
         pick = &t;
