@@ -143,10 +143,14 @@ KERNEL_SOURCES = ("compress_impl.cuh", "compress_launch.cuh", "compress_s4.cu",
 PROFILE = os.path.join(ROOT, "profiles", "compress_kernel_field-256MiB.md")
 
 
-def kernel_sources_sha() -> str:
+# The decompression kernel's sources (for its ncu figures).
+DECODE_SOURCES = ("decompress.cu", "glz_common.h", "glz_device.cuh", "launch_cache.cuh")
+
+
+def kernel_sources_sha(names=KERNEL_SOURCES) -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in names:
         with open(os.path.join(ROOT, "paper_2304_07342_gb300", "csrc", name), "rb") as f:
             h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()
@@ -164,6 +168,39 @@ def _profiled_traffic():
         return int(fields["dram_bytes_per_launch"].strip("` ")), "ncu capture " + os.path.basename(PROFILE)
     except (OSError, KeyError, ValueError):
         return None, "no ncu capture"
+
+
+def _profile_fields(name: str) -> dict:
+    """The `- `key: value`` lines of a committed ncu summary."""
+    try:
+        return {k.strip(): v.strip("` ") for k, v in
+                (line.strip().strip("- `").split(": ", 1) for line in
+                 open(os.path.join(ROOT, "profiles", name))
+                 if line.startswith("- `") and ": " in line)}
+    except OSError:
+        return {}
+
+
+def _issue_roofline(kernel: str, profile: str, sources, ms: float, n_sym: int,
+                    sms: int, mhz: float) -> dict:
+    """Instruction-issue roofline of a kernel bound by issue, not by memory:
+    warp instructions per launch (from the committed ncu summary, if it was
+    taken on the current sources) over the live launch time, against one
+    warp instruction per cycle per SM sub-partition (4 per SM) at the SM
+    clock."""
+    f = _profile_fields(profile)
+    out = {"kernel": kernel, "bound": "issue", "unit": "G warp-inst/s",
+           "peak": round(sms * 4 * mhz * 1e6 / 1e9, 1),
+           "peak_source": f"{sms} SMs x 4 sub-partitions x {mhz:.0f} MHz"}
+    if f.get("sources_sha256") != kernel_sources_sha(sources) or "warp_inst_per_launch" not in f:
+        return {**out, "achieved": None, "frac": None,
+                "note": "kernel changed since the ncu capture " + profile}
+    inst = int(f["warp_inst_per_launch"])
+    ach = inst / (ms * 1e-3) / 1e9
+    return {**out, "achieved": round(ach, 1), "frac": round(ach / out["peak"], 4),
+            "warp_inst_per_launch": inst, "warp_inst_per_symbol": round(inst / n_sym, 2),
+            "issue_active_pct_ncu": float(f.get("issue_active_pct", "nan")),
+            "source": "ncu capture " + profile}
 
 
 def _peaks():
@@ -347,7 +384,8 @@ def run_gpu(args):
             it[k] = None
     torch.cuda.empty_cache()
     if args.compressible:
-        line["compressible"] = _compressible(torch, codec, args, hbm_peak)
+        line["compressible"] = _compressible(torch, codec, args, hbm_peak,
+                                             line["clocks"].get("sm_max_mhz"))
     if args.paper_matcher:
         line["paper_matcher"] = _paper_matcher(torch, codec, args)
     if args.huffman:
@@ -392,7 +430,7 @@ def _time_codec(torch, codec, d, P, reps: int):
     return n / size, ev[0].elapsed_time(ev[1]) / reps, ev[1].elapsed_time(ev[2]) / reps, size
 
 
-def _compressible(torch, codec, args, hbm_peak: float):
+def _compressible(torch, codec, args, hbm_peak: float, sm_mhz=None):
     """Workloads with matches, where the parse and the decoder's pointer
     resolution do the work: the 1 MiB quantization codes of the small
     configuration (a single launch, bound by launch latency), 256 MiB of
@@ -400,14 +438,25 @@ def _compressible(torch, codec, args, hbm_peak: float):
     symbol-size sweep (1 GiB of first-order Markov codes stored as uint8,
     uint16 and uint32, C = 4096, W = 128).  Per input: compress and
     decompress GB/s (input bytes), the ratio, and each kernel's HBM fraction
-    counting the bytes it must move (input + stream)."""
+    counting the bytes it must move (input + stream).  For the 256 MiB of
+    quantization codes, where both kernels are bound by instruction issue,
+    also the issue roofline of each."""
     from paper_2304_07342_gb300 import lz, synth
     rows = []
+    issue = {}
 
     def run(name, x, P, reps):
         d = torch.from_numpy(np.ascontiguousarray(x).view(np.uint8).reshape(-1)).cuda()
         ratio, c_ms, d_ms, size = _time_codec(torch, codec, d, P, reps)
         n = d.numel()
+        if name == "uint16 quant codes 256 MiB":
+            sms = torch.cuda.get_device_properties(d.device).multi_processor_count
+            mhz = float(sm_mhz or 2070.0)
+            issue["compress"] = _issue_roofline("compress_kernel", "compress_kernel_quant-256MiB.md",
+                                                KERNEL_SOURCES, c_ms, n // P.S, sms, mhz)
+            issue["decompress"] = _issue_roofline("decompress_kernel",
+                                                  "decompress_kernel_quant-256MiB.md",
+                                                  DECODE_SOURCES, d_ms, n // P.S, sms, mhz)
         moved = n + size
         rows.append({"input": name, "bytes": n, "params": dict(zip("SCWmM", (P.S, P.C, P.W, P.m, P.M))),
                      "ratio": round(ratio, 4),
@@ -430,7 +479,7 @@ def _compressible(torch, codec, args, hbm_peak: float):
         del x
     del chain
     return {"workload": "quant codes (1 MiB, 256 MiB) and 1 GiB Markov codes at S = 1, 2, 4",
-            "peak_gbs": hbm_peak, "points": rows}
+            "peak_gbs": hbm_peak, "points": rows, "issue_roofline_quant_256MiB": issue}
 
 
 def _paper_matcher(torch, codec, args, n_sym: int = 128 << 20):

@@ -36,3 +36,21 @@ def test_reference_arm_line():
     # a step compresses whole chunks (or the whole input when it is shorter)
     n = int(cb["sample"].split("first ")[1].split(" bytes")[0])
     assert n > 0 and (n % 4096 == 0 or n == 1 << 20)
+
+
+def test_issue_roofline_from_committed_profiles():
+    """The issue roofline divides the ncu instruction count by the live time
+    and 4 warp instructions per SM per cycle; a profile taken on other
+    sources gives no figure."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench._issue_roofline("compress_kernel", "compress_kernel_quant-256MiB.md",
+                              bench.KERNEL_SOURCES, 2.0, 1 << 20, 152, 2000.0)
+    assert r["peak"] == 152 * 4 * 2000e6 / 1e9
+    if r["achieved"] is not None:  # the profile matches the sources
+        assert abs(r["achieved"] - r["warp_inst_per_launch"] / 2e-3 / 1e9) < 0.1
+        assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-3
+        assert r["warp_inst_per_symbol"] == round(r["warp_inst_per_launch"] / (1 << 20), 2)
+    other = bench._issue_roofline("decompress_kernel", "decompress_kernel_quant-256MiB.md",
+                                  bench.KERNEL_SOURCES, 1.0, 1 << 20, 152, 2000.0)
+    assert other["achieved"] is None and other["frac"] is None
