@@ -173,8 +173,9 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
 /* Compression from host memory to host memory: the same stream as
  * lz_compress of the same bytes, for callers whose data lives on the host.
  * h_in (n_bytes) and h_out (capacity out_cap) are host buffers.  The input
- * is copied to the device in pieces of whole index superblocks (64 chunks,
- * about 64 MiB a piece), and each piece is compressed by a launch over its
+ * is copied to the device in pieces of whole index superblocks (64 chunks;
+ * about 64 MiB a piece, smaller at both ends: 8, 16, 32 MiB first and
+ * last), and each piece is compressed by a launch over its
  * own chunks as soon as it has arrived, while the next piece is copied:
  * chunks are independent (section 3.3.1) and the look-back of a piece's
  * first chunks reaches into the pieces before it, which are complete.

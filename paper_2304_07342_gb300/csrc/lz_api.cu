@@ -402,7 +402,12 @@ lz_status compress_locked(lz_ctx *ctx, const void *d_in, uint64_t n_bytes, const
       round16(record_bound(C / S, S, off_bytes(p->window), p->min_match) + S + 16);
   const size_t status_end = kScratchHead + 8ull * nc;
   const size_t park_at = (status_end + 255) & ~static_cast<size_t>(255);
-  const size_t need = park_at + static_cast<size_t>(slot_bytes) * kParkSlots * wpb * grid;
+  // a launch over part of the chunks (one piece of lz_compress_host) keeps
+  // the status words of the launches before it, so the scratch must not be
+  // reallocated between them: it is sized for the largest grid
+  const uint64_t grid_room =
+      (c0 > 0 || c1 < nc) ? static_cast<uint64_t>(best_blocks) * ctx->sms : grid;
+  const size_t need = park_at + static_cast<size_t>(slot_bytes) * kParkSlots * wpb * grid_room;
   lz_status s = reserve_scratch(ctx, need);
   if (s != LZ_OK) return s;
   cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, clear_status ? status_end : kScratchHead, st);
@@ -449,6 +454,35 @@ lz_status compress_locked(lz_ctx *ctx, const void *d_in, uint64_t n_bytes, const
     default: e = glz::launch_compress_s4(A, nj, block, g, st); break;
   }
   return cuda_status(e);
+}
+
+// Piece sizes for lz_compress_host: whole multiples of `sb` except the last
+// (which takes the rest), growing from 8 MiB to 64 MiB at the start and
+// shrinking back to 8 MiB at the end.
+std::vector<uint64_t> host_pieces(uint64_t n, uint64_t sb) {
+  const auto whole = [&](uint64_t v) { return std::max<uint64_t>(sb, (v / sb) * sb); };
+  const uint64_t small = whole(8ull << 20), big = whole(64ull << 20);
+  std::vector<uint64_t> tail, out;
+  uint64_t left = (n / sb) * sb;  // the ragged rest joins the last piece
+  for (uint64_t s = small; left > 0 && s < big; s *= 2) {  // the end, last first
+    const uint64_t t = std::min(left, whole(s));
+    tail.push_back(t);
+    left -= t;
+  }
+  for (uint64_t s = small; left > 0 && s < big; s *= 2) {  // the start
+    const uint64_t t = std::min(left, whole(s));
+    out.push_back(t);
+    left -= t;
+  }
+  while (left > 0) {
+    const uint64_t t = std::min(left, big);
+    out.push_back(t);
+    left -= t;
+  }
+  out.insert(out.end(), tail.rbegin(), tail.rend());
+  if (out.empty()) out.push_back(0);
+  out.back() += n - (n / sb) * sb;
+  return out;
 }
 
 }  // namespace
@@ -513,16 +547,18 @@ lz_status lz_compress_host(lz_ctx *ctx, const void *h_in, uint64_t n_bytes, cons
   if (nc == 0) {
     st = compress_locked(ctx, d_in, 0, p, LZ_MATCH_EXACT, 1, d_out, cap, d_size, s_comp);
   } else {
-    // pieces of whole index superblocks, about 64 MiB: the copy of piece
-    // i + 1 overlaps the compression of piece i; a launch takes only its
-    // piece's chunks, and its look-back reaches into the pieces before it
-    // (4 MiB pieces measured 26 % slower end to end, 16 MiB 3 %: each
-    // piece costs a launch and an event wait)
+    // pieces of whole index superblocks: the copy of piece i + 1 overlaps
+    // the compression of piece i; a launch takes only its piece's chunks,
+    // and its look-back reaches into the pieces before it.  Pieces of about
+    // 64 MiB in the middle (4 MiB pieces throughout measured 26 % slower end
+    // to end, 16 MiB 3 %: each piece costs a launch and an event wait), but
+    // small at both ends, where nothing overlaps: compression starts once
+    // the first piece is in, and the call ends once the last one is written
     const uint64_t sb = glz::kIndexStride * static_cast<uint64_t>(C);
-    const uint64_t piece = std::max<uint64_t>(sb, ((64ull << 20) / sb) * sb);
-    const uint64_t npieces = div_up(n_bytes, piece);
-    for (uint64_t i = 0; i < npieces && st == LZ_OK; ++i) {
-      const uint64_t at = i * piece, len = std::min(piece, n_bytes - at);
+    const std::vector<uint64_t> pieces = host_pieces(n_bytes, sb);
+    uint64_t at = 0;
+    for (size_t i = 0; i < pieces.size() && st == LZ_OK; ++i) {
+      const uint64_t len = pieces[i];
       cudaEvent_t ev = ctx->hev[i % 8];
       if (cudaMemcpyAsync(d_in + at, static_cast<const uint8_t *>(h_in) + at, len,
                           cudaMemcpyHostToDevice, s_in) != cudaSuccess ||
@@ -533,6 +569,7 @@ lz_status lz_compress_host(lz_ctx *ctx, const void *h_in, uint64_t n_bytes, cons
       }
       st = compress_locked(ctx, d_in, n_bytes, p, LZ_MATCH_EXACT, 1, d_out, cap, d_size, s_comp,
                            at / C, (at + len) / C + ((at + len) % C ? 1 : 0), i == 0);
+      at += len;
     }
   }
   uint64_t size = 0;

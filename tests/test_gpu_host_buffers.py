@@ -1,5 +1,6 @@
 """lz_compress_host: host buffers in and out, compressed in overlapping
-pieces of whole index superblocks.  The stream must be byte-identical to the
+pieces of whole index superblocks (small at both ends, about 64 MiB in the
+middle).  The stream must be byte-identical to the
 CPU oracle's (and so to lz_compress of the same bytes): chunks are
 independent (section 3.3.1), so the pieces' records, table entries and
 rebased index entries are the whole input's."""
@@ -40,6 +41,10 @@ CASES = [
     ("markov u8, 2 KiB chunks", lambda: (synth.markov_codes(9_000_000, seed=3) % 256).astype(np.uint8),
      lz.Params(1, 2048, 300, 3, 255)),
     ("field f32", lambda: synth.gaussian_field((40, 128, 256), seed=5), lz.Params(4, 8192, 256, 2, 255)),
+    # pieces that grow (6, 16, 8 MiB and the rest): the scratch must keep
+    # the earlier pieces' look-back words
+    ("quant u16, 30 MiB in growing pieces", lambda: synth.quant_codes_laplace(15_728_640 + 999, seed=2),
+     lz.Params(2, 4096, 128, 3, 255)),
     ("one chunk", lambda: synth.quant_codes_laplace(1000, seed=1), lz.Params(2, 4096, 128, 3, 255)),
     ("empty", lambda: np.zeros(0, np.uint16), lz.Params(2, 4096, 128, 3, 255)),
 ]
