@@ -179,13 +179,14 @@ lz_status lz_compress_ex(lz_ctx *ctx, const void *d_in, uint64_t n_bytes,
  * own chunks as soon as it has arrived, while the next piece is copied:
  * chunks are independent (section 3.3.1) and the look-back of a piece's
  * first chunks reaches into the pieces before it, which are complete.
- * When h_out is pinned (cudaHostAlloc / cudaHostRegister, mapped into the
- * device's address space; on GB300 the NVLink-C2C link carries the
- * writes), the kernels write header, table, index and records straight to
- * their final places in it; otherwise the stream goes through a device
- * buffer and is copied out at the end.  Pinned h_in lets the copies overlap
- * the compression.  The context holds device memory for the input (and for
- * the stream when h_out is not pinned) between calls.  The call is
+ * The stream is built in device memory.  When h_out is pinned
+ * (cudaHostAlloc / cudaHostRegister), the records of each piece are copied
+ * to it as soon as the piece is done (the host reads where they end), on a
+ * third stream, while later pieces are copied in and compressed: the host
+ * link carries both directions at once; the header, table and index follow
+ * at the end.  Pageable h_out gets the stream in one copy at the end.
+ * Pinned h_in lets the copies overlap the compression.  The context holds
+ * device memory for the input and the stream between calls.  The call is
  * synchronous: it starts after the work already enqueued on `stream` and
  * returns when h_out holds the stream and *h_out_bytes (host) its size.
  * Device errors of this call are returned by it (and cleared), not left for

@@ -81,12 +81,14 @@ struct lz_ctx {
   uint32_t *d_err = nullptr;
   std::mutex mu;
   lz_test_hooks hooks{};    // test hooks (lz_set_test_hooks); all zero normally
-  // lz_compress_host: copy and compression streams, events, device memory
-  // (the input, a size word, the stream when the output is not mapped)
-  cudaStream_t hs[2] = {nullptr, nullptr};
-  cudaEvent_t hev[10] = {};
+  // lz_compress_host: copy-in, compression and copy-out streams, events,
+  // device memory (the input, a size word, the stream) and pinned host
+  // words (the look-back word of each piece's last chunk)
+  cudaStream_t hs[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t hev[17] = {};
   void *hdev = nullptr;
   size_t hdev_bytes = 0;
+  uint64_t *hpin = nullptr;
 };
 
 namespace {
@@ -95,6 +97,12 @@ constexpr int kCompressWarps = 4;      // warps per block (fewer if smem-bound)
 constexpr uint32_t kParkSlots = 3;     // parked records per compressing warp
 constexpr int kDecompressBlock = 1024;  // up to 32 warps, one chunk per warp at a time
 constexpr size_t kScratchHead = 16;
+// The look-back word of a placed chunk (written by the compression kernel):
+// bit 63 set, the inclusive prefix of the record bytes in the low 62 bits.
+constexpr uint64_t kStatusPrefix = 1ull << 63, kStatusValue = (1ull << 62) - 1;
+// lz_compress_host: pieces queued on the GPU ahead of the one whose records
+// the host copies out next (less than the 8 event and word slots)
+constexpr size_t kHostLag = 6;
 // Chunks per compression launch: the warps take chunks from a 32-bit work
 // counter and each takes one ticket past the last chunk, so the counter must
 // not wrap; the margin covers 2^20 warps.
@@ -320,6 +328,7 @@ void lz_destroy(lz_ctx *ctx) {
   for (cudaEvent_t &e : ctx->hev)
     if (e) cudaEventDestroy(e);
   if (ctx->hdev) cudaFree(ctx->hdev);
+  if (ctx->hpin) cudaFreeHost(ctx->hpin);
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->d_err) cudaFree(ctx->d_err);
   delete ctx;
@@ -504,26 +513,30 @@ lz_status lz_compress_host(lz_ctx *ctx, const void *h_in, uint64_t n_bytes, cons
   std::lock_guard<std::mutex> lock(ctx->mu);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return LZ_ERR_CUDA;
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
     if (!ctx->hs[i]) e = cudaStreamCreateWithFlags(&ctx->hs[i], cudaStreamNonBlocking);
-  for (int i = 0; i < 10 && e == cudaSuccess; ++i)
+  for (int i = 0; i < 17 && e == cudaSuccess; ++i)
     if (!ctx->hev[i]) e = cudaEventCreateWithFlags(&ctx->hev[i], cudaEventDisableTiming);
+  if (e == cudaSuccess && !ctx->hpin)
+    e = cudaHostAlloc(reinterpret_cast<void **>(&ctx->hpin), 8 * sizeof(uint64_t),
+                      cudaHostAllocDefault);
   if (e != cudaSuccess) return cuda_status(e);
-  // the output: written by the kernel in place when the host buffer is
-  // mapped into the device's address space (pinned memory), else through a
-  // device buffer copied out at the end
-  uint8_t *d_out = nullptr;
+  // The stream is built in device memory.  A pinned h_out gets it piece by
+  // piece: once a piece's launch is done, the look-back word of its last
+  // chunk gives the end of the records written so far, and a copy on a
+  // third stream takes them to h_out while later pieces are copied in and
+  // compressed (copy engines in both directions: the host link carries
+  // both at once).  A pageable h_out gets one copy at the end.
+  bool pinned = false;
   {
     cudaPointerAttributes at{};
-    if (cudaPointerGetAttributes(&at, h_out) == cudaSuccess && at.type == cudaMemoryTypeHost &&
-        at.devicePointer)
-      d_out = static_cast<uint8_t *>(at.devicePointer);
+    pinned = cudaPointerGetAttributes(&at, h_out) == cudaSuccess &&
+             at.type == cudaMemoryTypeHost;
     cudaGetLastError();  // clear a lookup error of an unregistered pointer
   }
-  // device memory: the input, a size word and (unmapped output) the stream
   const uint64_t in_room = (n_bytes + 255) & ~255ull;
-  const uint64_t out_room = d_out ? 0 : ((std::min(out_cap, lz_compressed_bound(n_bytes, p)) +
-                                          255) & ~255ull);
+  const uint64_t cap = std::min(out_cap, lz_compressed_bound(n_bytes, p));
+  const uint64_t out_room = (cap + 255) & ~255ull;
   const uint64_t want = in_room + 256 + out_room;
   if (ctx->hdev_bytes < want) {
     if (ctx->hooks.fail_alloc) return LZ_ERR_NOMEM;
@@ -535,14 +548,44 @@ lz_status lz_compress_host(lz_ctx *ctx, const void *h_in, uint64_t n_bytes, cons
   }
   uint8_t *d_in = static_cast<uint8_t *>(ctx->hdev);
   auto *d_size = reinterpret_cast<unsigned long long *>(d_in + in_room);
-  const uint64_t cap = d_out ? out_cap : out_room;
-  if (!d_out) d_out = d_in + in_room + 256;
-  cudaStream_t s_in = ctx->hs[0], s_comp = ctx->hs[1];
-  cudaEvent_t ev_start = ctx->hev[9];
+  uint8_t *d_out = d_in + in_room + 256;
+  uint8_t *hb = static_cast<uint8_t *>(h_out);
+  cudaStream_t s_in = ctx->hs[0], s_comp = ctx->hs[1], s_out = ctx->hs[2];
+  cudaEvent_t ev_start = ctx->hev[16];
   if (cudaEventRecord(ev_start, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess ||
       cudaStreamWaitEvent(s_in, ev_start, 0) != cudaSuccess ||
-      cudaStreamWaitEvent(s_comp, ev_start, 0) != cudaSuccess)
+      cudaStreamWaitEvent(s_comp, ev_start, 0) != cudaSuccess ||
+      cudaStreamWaitEvent(s_out, ev_start, 0) != cudaSuccess)
     return LZ_ERR_CUDA;
+  // records [records_at, copied) are on their way to h_out
+  uint64_t copied = records_at;
+  bool copying = pinned;
+  // piece j is done: copy the records it completed (from a 64-byte boundary:
+  // the bytes before are final or rewritten by the copy of the table at the
+  // end)
+  auto flush = [&](size_t j) {
+    if (!copying) return;
+    cudaEvent_t done = ctx->hev[8 + j % 8];
+    if (cudaEventSynchronize(done) != cudaSuccess) {
+      copying = false;
+      return;
+    }
+    const uint64_t w = ctx->hpin[j % 8];
+    if (!(w & kStatusPrefix)) {  // not placed: a device error, reported below
+      copying = false;
+      return;
+    }
+    const uint64_t end = std::min(cap, records_at + (w & kStatusValue));
+    if (end <= copied) return;
+    const uint64_t from = copied & ~63ull;
+    if (cudaStreamWaitEvent(s_out, done, 0) != cudaSuccess ||
+        cudaMemcpyAsync(hb + from, d_out + from, end - from, cudaMemcpyDeviceToHost, s_out) !=
+            cudaSuccess) {
+      copying = false;
+      return;
+    }
+    copied = end;
+  };
   lz_status st = LZ_OK;
   if (nc == 0) {
     st = compress_locked(ctx, d_in, 0, p, LZ_MATCH_EXACT, 1, d_out, cap, d_size, s_comp);
@@ -553,12 +596,13 @@ lz_status lz_compress_host(lz_ctx *ctx, const void *h_in, uint64_t n_bytes, cons
     // 64 MiB in the middle (4 MiB pieces throughout measured 26 % slower end
     // to end, 16 MiB 3 %: each piece costs a launch and an event wait), but
     // small at both ends, where nothing overlaps: compression starts once
-    // the first piece is in, and the call ends once the last one is written
+    // the first piece is in, and the call ends once the last one is out
     const uint64_t sb = glz::kIndexStride * static_cast<uint64_t>(C);
     const std::vector<uint64_t> pieces = host_pieces(n_bytes, sb);
     uint64_t at = 0;
     for (size_t i = 0; i < pieces.size() && st == LZ_OK; ++i) {
       const uint64_t len = pieces[i];
+      const uint64_t c0 = at / C, c1 = (at + len) / C + ((at + len) % C ? 1 : 0);
       cudaEvent_t ev = ctx->hev[i % 8];
       if (cudaMemcpyAsync(d_in + at, static_cast<const uint8_t *>(h_in) + at, len,
                           cudaMemcpyHostToDevice, s_in) != cudaSuccess ||
@@ -568,9 +612,25 @@ lz_status lz_compress_host(lz_ctx *ctx, const void *h_in, uint64_t n_bytes, cons
         break;
       }
       st = compress_locked(ctx, d_in, n_bytes, p, LZ_MATCH_EXACT, 1, d_out, cap, d_size, s_comp,
-                           at / C, (at + len) / C + ((at + len) % C ? 1 : 0), i == 0);
+                           c0, c1, i == 0);
       at += len;
+      if (st != LZ_OK || !pinned) continue;
+      // the look-back word of the piece's last chunk (its records' end)
+      const auto *word = reinterpret_cast<const uint64_t *>(
+          static_cast<const uint8_t *>(ctx->scratch) + kScratchHead + 8 * (c1 - 1));
+      if (cudaMemcpyAsync(&ctx->hpin[i % 8], word, 8, cudaMemcpyDeviceToHost, s_comp) !=
+              cudaSuccess ||
+          cudaEventRecord(ctx->hev[8 + i % 8], s_comp) != cudaSuccess) {
+        st = LZ_ERR_CUDA;
+        break;
+      }
+      // the host waits for the oldest piece whose records are not on their
+      // way yet, while the GPU has the next pieces queued
+      if (i >= kHostLag) flush(i - kHostLag);
     }
+    for (size_t j = pieces.size() > kHostLag ? pieces.size() - kHostLag : 0;
+         st == LZ_OK && pinned && j < pieces.size(); ++j)
+      flush(j);
   }
   uint64_t size = 0;
   if (st == LZ_OK &&
@@ -594,11 +654,25 @@ lz_status lz_compress_host(lz_ctx *ctx, const void *h_in, uint64_t n_bytes, cons
            : (h & glz::kErrCorrupt) ? LZ_ERR_CORRUPT
                                     : LZ_ERR_BUFFER_TOO_SMALL;
   }
-  if (st != LZ_OK) return st;
+  if (st != LZ_OK) {
+    cudaStreamSynchronize(s_out);
+    return st;
+  }
   *h_out_bytes = size;
-  if (size > out_cap) return LZ_ERR_BUFFER_TOO_SMALL;
-  if (out_room && cudaMemcpy(h_out, d_out, size, cudaMemcpyDeviceToHost) != cudaSuccess)
-    return LZ_ERR_CUDA;  // the stream went through a device buffer
+  if (size > out_cap) {
+    cudaStreamSynchronize(s_out);
+    return LZ_ERR_BUFFER_TOO_SMALL;
+  }
+  // the header, table and index (final now), and any records not yet copied
+  const uint64_t head = std::min<uint64_t>(records_at, size);
+  bool ok = cudaMemcpyAsync(hb, d_out, head, cudaMemcpyDeviceToHost, s_out) == cudaSuccess;
+  if (ok && size > copied && pinned)
+    ok = cudaMemcpyAsync(hb + copied, d_out + copied, size - copied, cudaMemcpyDeviceToHost,
+                         s_out) == cudaSuccess;
+  if (ok && !pinned && size > head)
+    ok = cudaMemcpyAsync(hb + head, d_out + head, size - head, cudaMemcpyDeviceToHost, s_out) ==
+         cudaSuccess;
+  if (cudaStreamSynchronize(s_out) != cudaSuccess || !ok) return LZ_ERR_CUDA;
   return LZ_OK;
 }
 
