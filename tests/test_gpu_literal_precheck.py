@@ -5,7 +5,8 @@ stream: streams stay byte-identical to the oracle's.
 The inputs are random symbols (no repeats, so the pre-check is taken) with
 one planted repeat of m or more symbols, placed where the exactness
 argument is delicate: source and target in one 32-position slab (either
-order of the atomic unit), in adjacent slabs, at offsets just inside and
+order of the atomic unit), in adjacent slabs, in one group of 8 slabs or
+across two, at offsets just inside and
 just outside the window, shorter than m, overlapping (offset < m), and at
 the very end of the chunk.  Random data with many near-duplicate keys (small
 alphabets in the high bytes) exercises the exact check of flagged
@@ -54,7 +55,11 @@ for S, C, W, m in ((4, 8192, 256, 2), (4, 4096, 128, 1), (4, 8192, 256, 3),
     for tgt, d, ln in ((40, 5, m), (37, 3, m + 2), (70, 40, m), (64, 1, 4), (63, 2, 4),
                        (300, W, m), (300, W + 1, m), (500, W - 1, m + 1),
                        (k - m, 17, m), (k - m, W, m), (100, 9, max(1, m - 1)),
-                       (33, 31, m), (95, 31, m), (31, 30, m)):
+                       (33, 31, m), (95, 31, m), (31, 30, m),
+                       # farther apart inside the first 8 slabs, and across
+                       # their end
+                       (200, 100, m), (255, 200, m), (250, 60, m + 1), (260, 10, m),
+                       (290, 250, m), (511, 255, m)):
         CASES.append((S, C, W, m, tgt, d, ln))
 
 
