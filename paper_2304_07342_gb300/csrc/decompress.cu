@@ -307,17 +307,18 @@ __device__ __forceinline__ bool decode_tokens(const Header &h, const uint8_t *fl
       const uint32_t lenB = mB ? (wB & 0xFFu) : (vB ? 1u : 0u);
       const uint32_t offA = mA ? ((wA >> 8) & offmask) + 1u : 0u;
       const uint32_t offB = mB ? ((wB >> 8) & offmask) + 1u : 0u;
-      uint32_t xA = lenA, xB = lenB;  // inclusive scans of token lengths
+      // inclusive scans of both groups' token lengths in one: A in the low
+      // and B in the high 16 bits (a group's lengths sum to at most
+      // 32 x 255, so the halves never carry into each other)
+      uint32_t x = lenA | (lenB << 16);
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t yA = __shfl_up_sync(kFull, xA, o);
-        const uint32_t yB = __shfl_up_sync(kFull, xB, o);
-        if (lane >= static_cast<uint32_t>(o)) {
-          xA += yA;
-          xB += yB;
-        }
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= static_cast<uint32_t>(o)) x += y;
       }
-      const uint32_t glA = __shfl_sync(kFull, xA, 31), glB = __shfl_sync(kFull, xB, 31);
+      const uint32_t gl2 = __shfl_sync(kFull, x, 31);
+      const uint32_t xA = x & 0xFFFFu, xB = x >> 16;
+      const uint32_t glA = gl2 & 0xFFFFu, glB = gl2 >> 16;
       const uint32_t sA = pos + xA - lenA, sB = pos + glA + xB - lenB;
       // a pointer needs 1 <= length <= offset (any length <= 255 in overlap
       // mode) and offset <= min(W, its start): its source lies in the chunk
@@ -350,16 +351,13 @@ __device__ __forceinline__ bool decode_tokens(const Header &h, const uint8_t *fl
     carry = __shfl_sync(kFull, own, 31);
     const bool ptr = act && own != 0;
     uint32_t f = ptr ? j - own : j;
-    if (__any_sync(kFull, ptr && f >= r0)) {
-      // sources inside this round: jump until every source is a literal of
-      // the round or lies before it (chains shrink, so at most 5 rounds)
-      while (true) {
-        const uint32_t g = __shfl_sync(kFull, f, f >= r0 ? f - r0 : lane);
-        const bool moved = g != f;
-        f = g;
-        if (!__any_sync(kFull, moved)) break;
-      }
-    }
+    // sources inside this round that are pointer symbols themselves are not
+    // final yet: jump (f <- the source's source, all lanes at once) until
+    // every source is a literal of the round or lies before it (chains
+    // shrink, so at most 5 turns)
+    const uint32_t pm = __ballot_sync(kFull, ptr);
+    auto pending = [&](uint32_t x) { return x >= r0 && ((pm >> (x - r0)) & 1u); };
+    while (__any_sync(kFull, pending(f))) f = __shfl_sync(kFull, f, pending(f) ? f - r0 : lane);
     if (ptr && GLZ_OK(f < j)) st_slot<S>(ob, j, ld_slot<S>(ob, f, aligned), aligned);
     __syncwarp();
   }
