@@ -237,7 +237,9 @@ __device__ __forceinline__ uint32_t flag_word(const uint8_t *flags, uint32_t g, 
 // memory (words may be read up to 3 bytes past it).  False when the tokens
 // are inconsistent (corrupt stream); nothing outside the chunk's output and
 // the slice is written either way.
-template <int S, bool STAGED>
+// SAME: a pointer's payload is S bytes like a literal's (1 + offB == S), so
+// token t's payload starts at S * t without counting the pointers before it.
+template <int S, bool STAGED, bool SAME = false>
 __device__ __forceinline__ bool decode_tokens(const Header &h, const uint8_t *flags,
                                               const uint8_t *payload, uint32_t ntok,
                                               uint32_t pay_tok, uint32_t k, uint8_t *ob,
@@ -275,26 +277,33 @@ __device__ __forceinline__ bool decode_tokens(const Header &h, const uint8_t *fl
   uint32_t pos = 0, pdone = 0;  // symbols produced; pointers in earlier blocks of groups
   for (uint32_t g0 = 0; g0 < ngroups; g0 += 32) {
     const uint32_t fwr = g0 + lane < ngroups ? flag_word<STAGED>(flags, g0 + lane, ntok, fb) : 0u;
-    const uint32_t cnt = __popc(fwr);
-    uint32_t incl = cnt;
+    uint32_t pb = 0;  // pointers before group g0 + lane (not needed when SAME)
+    if constexpr (!SAME) {
+      const uint32_t cnt = __popc(fwr);
+      uint32_t incl = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, incl, o);
-      if (lane >= static_cast<uint32_t>(o)) incl += y;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= static_cast<uint32_t>(o)) incl += y;
+      }
+      pb = pdone + incl - cnt;
+      pdone += __shfl_sync(kFull, incl, 31);
     }
-    const uint32_t pb = pdone + incl - cnt;  // pointers before group g0 + lane
-    pdone += __shfl_sync(kFull, incl, 31);
     const uint32_t nblk = min(32u, ngroups - g0);
     for (uint32_t i = 0; i < nblk; i += 2) {
       const bool hasB = i + 1 < nblk;
-      const uint32_t fwA = __shfl_sync(kFull, fwr, i), pbA = __shfl_sync(kFull, pb, i);
+      const uint32_t fwA = __shfl_sync(kFull, fwr, i);
       const uint32_t fwB = __shfl_sync(kFull, fwr, (i + 1) & 31u);
-      const uint32_t pbB = __shfl_sync(kFull, pb, (i + 1) & 31u);
       const uint32_t tA = (g0 + i) * 32 + lane, tB = tA + 32;
       const bool vA = tA < ntok, vB = hasB && tB < ntok;
       const bool mA = (fwA >> lane) & 1u, mB = hasB && ((fwB >> lane) & 1u);
-      const uint32_t nbA = pbA + __popc(fwA & lt), nbB = pbB + __popc(fwB & lt);
-      const uint32_t oA = S * (tA - nbA) + tsz * nbA, oB = S * (tB - nbB) + tsz * nbB;
+      uint32_t oA = S * tA, oB = S * tB;
+      if constexpr (!SAME) {
+        const uint32_t pbA = __shfl_sync(kFull, pb, i), pbB = __shfl_sync(kFull, pb, (i + 1) & 31u);
+        const uint32_t nbA = pbA + __popc(fwA & lt), nbB = pbB + __popc(fwB & lt);
+        oA = S * (tA - nbA) + tsz * nbA;
+        oB = S * (tB - nbB) + tsz * nbB;
+      }
       uint32_t wA = 0, wB = 0;
       if constexpr (STAGED) {
         if (vA && GLZ_OK(oA < pay_tok)) wA = ld_u32_any(payload + oA);
@@ -373,6 +382,9 @@ __device__ __forceinline__ bool decode_tokens_s(const Header &h, const uint8_t *
     case 1:
       return decode_tokens<1, STAGED>(h, flags, payload, ntok, pay_tok, k, ob, aligned, sl, lane);
     case 2:
+      if (h.offB == 1)  // a pointer (length, offset - 1) is two bytes, as a symbol
+        return decode_tokens<2, STAGED, true>(h, flags, payload, ntok, pay_tok, k, ob, aligned, sl,
+                                              lane);
       return decode_tokens<2, STAGED>(h, flags, payload, ntok, pay_tok, k, ob, aligned, sl, lane);
     default:
       return decode_tokens<4, STAGED>(h, flags, payload, ntok, pay_tok, k, ob, aligned, sl, lane);
