@@ -350,13 +350,21 @@ __device__ __forceinline__ bool decode_tokens(const Header &h, const uint8_t *fl
     const uint32_t j = r0 + lane;
     const bool act = j < k;
     const uint32_t mk = marks[j];  // zero past k
-    const uint32_t sw = __ballot_sync(kFull, mk != 0), mw = __ballot_sync(kFull, mk == 2);
-    uint32_t raw = act ? ld_slot<S>(ob, j, aligned) : 0u;
-    if (S == 1 && sl.hi && act) raw |= static_cast<uint32_t>(sl.hi[j]) << 8;
+    const uint32_t sw = __ballot_sync(kFull, mk != 0);
+    // the offset of the pointer starting here (its slot holds offset - 1);
+    // 0 at a literal's start
+    uint32_t so = 0;
+    if constexpr (S == 1) {  // (a byte load costs less than the branch around it)
+      uint32_t raw = act ? ld_slot<S>(ob, j, aligned) : 0u;
+      if (sl.hi && act) raw |= static_cast<uint32_t>(sl.hi[j]) << 8;
+      so = mk == 2 ? raw + 1u : 0u;
+    } else if (mk == 2) {
+      so = ld_slot<S>(ob, j, aligned) + 1u;
+    }
     const uint32_t mb = sw & le;
     const uint32_t ol = (31u - __clz(mb)) & 31u;  // owner's lane when mb != 0
-    const uint32_t oraw = __shfl_sync(kFull, raw, ol);
-    const uint32_t own = mb ? (((mw >> ol) & 1u) ? oraw + 1u : 0u) : carry;
+    const uint32_t oso = __shfl_sync(kFull, so, ol);
+    const uint32_t own = mb ? oso : carry;
     carry = __shfl_sync(kFull, own, 31);
     const bool ptr = act && own != 0;
     uint32_t f = ptr ? j - own : j;
